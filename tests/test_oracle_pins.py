@@ -1,0 +1,444 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the paper's
+Figure 1 (golden file), exact rational identities of the lattices, closed-form
+flows (Taylor-Green, Poiseuille, Couette), conservation laws, brute-force loops
+on tiny grids, special cases (gamma = 2 KBC is BGK, omega = 1 BGK gives f^eq),
+the KBC entropy condition, the D2Q9 KBC shear part in its closed form, and
+complex-step / finite-difference derivatives for the adjoint.
+"""
+import itertools
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import lbm as O
+from paper_2311_16080_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "lattice_velocities.txt")
+
+
+def _read_golden():
+    sets, cur = {}, None
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("["):
+            cur = line.strip("[]")
+            sets[cur] = []
+        else:
+            sets[cur].append(tuple(int(v) for v in line.split()))
+    return sets
+
+
+@pytest.mark.parametrize("q", [9, 19, 27])
+def test_velocity_order_matches_figure_1(q):
+    gold = _read_golden()[f"D{2 if q == 9 else 3}Q{q}"]
+    lat = O.Lattice(q)
+    assert [tuple(int(v) for v in c) for c in lat.c[1:]] == gold
+    assert all(v == 0 for v in lat.c[0])
+    assert len(set(map(tuple, lat.c))) == q
+
+
+@pytest.mark.parametrize("q", [9, 19, 27])
+def test_lattice_isotropy_exact(q):
+    """sum w = 1, odd moments vanish, sum w c_a c_b = d_ab/3,
+    sum w c_a c_b c_c c_d = (d_ab d_cd + d_ac d_bd + d_ad d_bc)/9, in rationals."""
+    lat = O.Lattice(q)
+    w = lat.w_frac
+    c = [tuple(int(v) for v in ci) for ci in lat.c]
+    d = lat.d
+    assert sum(w) == 1
+    delta = lambda a, b: Fraction(int(a == b))
+    for a in range(d):
+        assert sum(w[i] * c[i][a] for i in range(q)) == 0
+    for a, b in itertools.product(range(d), repeat=2):
+        assert sum(w[i] * c[i][a] * c[i][b] for i in range(q)) == delta(a, b) / 3
+    for a, b, e in itertools.product(range(d), repeat=3):
+        assert sum(w[i] * c[i][a] * c[i][b] * c[i][e] for i in range(q)) == 0
+    for a, b, e, g in itertools.product(range(d), repeat=4):
+        lhs = sum(w[i] * c[i][a] * c[i][b] * c[i][e] * c[i][g] for i in range(q))
+        rhs = (delta(a, b) * delta(e, g) + delta(a, e) * delta(b, g) + delta(a, g) * delta(b, e)) / 9
+        assert lhs == rhs
+    for i in range(q):
+        assert all(lat.c[lat.opp[i]] == -lat.c[i])
+
+
+@pytest.mark.parametrize("q", [9, 19, 27])
+def test_equilibrium_moments(q):
+    """sum f^eq = rho, sum c f^eq = rho u, sum c_a c_b f^eq = rho (cs2 d_ab + u_a u_b)."""
+    lat = O.Lattice(q)
+    rng = np.random.default_rng(5)
+    shape = (3, 4) if lat.d == 2 else (2, 3, 4)
+    rho = 1 + 0.1 * rng.uniform(-1, 1, shape)
+    u = 0.1 * rng.uniform(-1, 1, (lat.d,) + shape)
+    feq = O.equilibrium(lat, rho, u)
+    np.testing.assert_allclose(feq.sum(0), rho, rtol=1e-15, atol=0)
+    for a in range(lat.d):
+        np.testing.assert_allclose(np.tensordot(lat.c[:, a], feq, (0, 0)), rho * u[a],
+                                   rtol=1e-13, atol=1e-16)
+        for b in range(lat.d):
+            m2 = np.tensordot(lat.c[:, a] * lat.c[:, b], feq, (0, 0))
+            np.testing.assert_allclose(m2, rho * ((a == b) / 3 + u[a] * u[b]), rtol=1e-14, atol=1e-16)
+
+
+def test_bgk_omega_one_gives_equilibrium():
+    lat = O.Lattice(19)
+    rho, u = I.random_flow((3, 4, 5), 3, seed=1)
+    f = O.equilibrium(lat, rho, u) * (1 + 0.01 * np.random.default_rng(2).uniform(-1, 1, (19, 3, 4, 5)))
+    r = O.density(lat, f)
+    uu = O.momentum(lat, f) / r
+    np.testing.assert_allclose(O.collide_bgk(lat, f, 1.0), O.equilibrium(lat, r, uu), rtol=1e-14)
+
+
+def _perturbed_state(lat, shape, seed):
+    rho, u = I.random_flow(shape, lat.d, seed=seed, rho_amp=0.02, u_amp=0.05)
+    f = O.equilibrium(lat, rho, u)
+    rng = np.random.default_rng(seed + 100)
+    return f * (1 + 0.02 * rng.uniform(-1, 1, f.shape))
+
+
+@pytest.mark.parametrize("q,coll,shape,steps", [
+    (9, "bgk", (16, 16), 1000),
+    (19, "bgk", (6, 7, 8), 150),
+    (27, "kbc", (5, 6, 7), 150),
+    (9, "kbc", (12, 10), 500),
+])
+def test_conservation_periodic(q, coll, shape, steps):
+    """Collision and periodic streaming conserve mass and momentum."""
+    lat = O.Lattice(q)
+    mask = np.zeros(shape, np.uint8)
+    p = O.Params(lat, 1.6, collision=coll)
+    f = _perturbed_state(lat, shape, seed=q)
+    m0, j0 = O.total_mass(lat, f, mask), O.total_momentum(lat, f, mask)
+    f = O.run(lat, f, mask, p, steps)
+    m1, j1 = O.total_mass(lat, f, mask), O.total_momentum(lat, f, mask)
+    assert abs(m1 - m0) <= 1e-12 * abs(m0)
+    for a in range(lat.d):
+        assert abs(j1[a] - j0[a]) <= 1e-12 * abs(m0)
+
+
+def test_stream_only_is_a_permutation_bruteforce():
+    """With no collision, n steps move f_i by n c_i (mod the grid): checked
+    bit-exactly against per-cell Python loops."""
+    lat = O.Lattice(19)
+    nz, ny, nx = 3, 4, 5
+    rng = np.random.default_rng(7)
+    f0 = rng.standard_normal((19, nz, ny, nx))
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    p = O.Params(lat, 1.0, collision="none")
+    n = 3
+    f = O.run(lat, f0, mask, p, n)
+    for i in range(19):
+        cx, cy, cz = (int(v) for v in lat.c[i])
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    src = f0[i, (z - n * cz) % nz, (y - n * cy) % ny, (x - n * cx) % nx]
+                    assert f[i, z, y, x] == src
+
+
+def test_pull_rules_bruteforce():
+    """WALL / LID / EQ substitution of the pull, against per-cell loops."""
+    lat = O.Lattice(9)
+    ny, nx = 5, 6
+    rng = np.random.default_rng(11)
+    mask = rng.choice([O.FLUID, O.FLUID, O.FLUID, O.WALL, O.LID, O.EQ], size=(ny, nx)).astype(np.uint8)
+    h = rng.standard_normal((9, ny, nx))
+    bc = O.BC(2, lid_u=(0.03, -0.02), lid_rho=1.0, eq_rho=1.01, eq_u=(0.01, 0.02))
+    f = O.pull_plain(lat, h, mask, bc)
+    w = [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
+    for i in range(9):
+        cx, cy = (int(v) for v in lat.c[i])
+        for y in range(ny):
+            for x in range(nx):
+                t = mask[(y - cy) % ny, (x - cx) % nx]
+                o = int(lat.opp[i])
+                if t == O.WALL:
+                    ref = h[o, y, x]
+                elif t == O.LID:
+                    ref = h[o, y, x] + 6 * w[i] * 1.0 * (cx * 0.03 + cy * -0.02)
+                elif t == O.EQ:
+                    cu = cx * 0.01 + cy * 0.02
+                    ref = w[i] * 1.01 * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (0.01 ** 2 + 0.02 ** 2))
+                else:
+                    ref = h[i, (y - cy) % ny, (x - cx) % nx]
+                assert abs(f[i, y, x] - ref) <= 1e-15 * max(1.0, abs(ref))
+
+
+def test_kbc_gamma_two_is_bgk():
+    for q, shape in ((9, (5, 6)), (27, (3, 4, 5))):
+        lat = O.Lattice(q)
+        f = _perturbed_state(lat, shape, seed=3)
+        np.testing.assert_allclose(O.collide_kbc(lat, f, 1.7, gamma=2.0),
+                                   O.collide_bgk(lat, f, 1.7), rtol=1e-13, atol=1e-16)
+
+
+@pytest.mark.parametrize("q", [9, 27])
+def test_kbc_entropy_condition(q):
+    """The entropic gamma makes the post-collision non-equilibrium part
+    orthogonal to dh in the 1/f^eq inner product (stationary point of the
+    quadratic entropy), and KBC conserves rho and j."""
+    lat = O.Lattice(q)
+    shape = (5, 6) if q == 9 else (3, 4, 5)
+    f = _perturbed_state(lat, shape, seed=9)
+    omega = 1.9
+    fs = O.collide_kbc(lat, f, omega)
+    rho = O.density(lat, f)
+    u = O.momentum(lat, f) / rho
+    feq = O.equilibrium(lat, rho, u)
+    ds = O.kbc_shear_part(lat, f - feq)
+    dh = (f - feq) - ds
+    inner = ((fs - feq) * dh / feq).sum(0)
+    scale = (dh * dh / feq).sum(0)
+    assert np.max(np.abs(inner) / scale) < 1e-9
+    np.testing.assert_allclose(O.density(lat, fs), rho, rtol=1e-14)
+    np.testing.assert_allclose(O.momentum(lat, fs), O.momentum(lat, f), atol=1e-15)
+    g = O.kbc_gamma(lat, ds, dh, feq, omega / 2)
+    assert not np.allclose(g, 2.0)  # the entropic value differs from BGK here
+
+
+def test_kbc_d2q9_shear_part_closed_form():
+    """D2Q9 KBC shear populations (Karlin et al. 2014): s_(+-1,0) = N/4,
+    s_(0,+-1) = -N/4, s_(s,l) = s l Pxy / 4, s_rest = 0, where N = Pxx - Pyy and
+    Pxy are the raw second moments of the field."""
+    lat = O.Lattice(9)
+    g = np.random.default_rng(4).standard_normal((9, 3, 3))
+    cx, cy = lat.c[:, 0], lat.c[:, 1]
+    pxx = np.tensordot(cx * cx, g, (0, 0))
+    pyy = np.tensordot(cy * cy, g, (0, 0))
+    pxy = np.tensordot(cx * cy, g, (0, 0))
+    N = pxx - pyy
+    s = O.kbc_shear_part(lat, g)
+    for i in range(9):
+        a, b = int(cx[i]), int(cy[i])
+        if a == 0 and b == 0:
+            ref = 0 * N
+        elif b == 0:
+            ref = N / 4
+        elif a == 0:
+            ref = -N / 4
+        else:
+            ref = a * b * pxy / 4
+        np.testing.assert_allclose(s[i], ref, atol=1e-14)
+
+
+def test_kbc_d3q27_shear_part_moments():
+    """The D3Q27 shear part carries the deviatoric second moments of g and
+    has zero mass, momentum, trace, and zero weight on the eight corners."""
+    lat = O.Lattice(27)
+    g = np.random.default_rng(8).standard_normal((27, 2, 2, 2))
+    s = O.kbc_shear_part(lat, g)
+    c = lat.c.astype(float)
+    P = lambda fld, a, b: np.tensordot(c[:, a] * c[:, b], fld, (0, 0))
+    trg = sum(P(g, a, a) for a in range(3))
+    for a in range(3):
+        for b in range(3):
+            ref = P(g, a, b) - (a == b) * trg / 3
+            np.testing.assert_allclose(P(s, a, b), ref, atol=1e-13)
+    np.testing.assert_allclose(s.sum(0), 0, atol=1e-13)
+    for a in range(3):
+        np.testing.assert_allclose(np.tensordot(c[:, a], s, (0, 0)), 0, atol=1e-13)
+    corners = [i for i in range(27) if np.all(lat.c[i] != 0)]
+    np.testing.assert_allclose(s[corners], 0, atol=1e-15)
+
+
+def _tg_amplitude(lat, coll, n, steps, omega=1.25):
+    rho, u = I.taylor_green_2d(n, n, u0=0.04)
+    mask = np.zeros((n, n), np.uint8)
+    p = O.Params(lat, omega, collision=coll)
+    f = O.run(lat, O.init_state(lat, rho, u, mask, p), mask, p, steps)
+    _, uu = O.macroscopic(lat, f, mask, p)
+    amp = float((uu * u).sum() / (u * u).sum())
+    return amp, I.taylor_green_amplitude_factor(steps, O.nu_from_omega(omega), n, n)
+
+
+def test_taylor_green_decay_bgk():
+    """D2Q9 BGK Taylor-Green, 128^2, omega = 1.25, 1000 steps: the velocity
+    amplitude follows the closed-form viscous decay within 1% (Section 4.1)."""
+    amp, ref = _tg_amplitude(O.Lattice(9), "bgk", 128, 1000)
+    assert abs(amp / ref - 1) < 0.01
+
+
+def test_taylor_green_decay_kbc():
+    amp, ref = _tg_amplitude(O.Lattice(9), "kbc", 64, 400)
+    assert abs(amp / ref - 1) < 0.01
+
+
+def _poiseuille(H, omega, F=1e-5, steps=2000):
+    lat = O.Lattice(9)
+    mask = I.channel_2d_mask(4, H + 2)
+    nu = O.nu_from_omega(omega)
+    p = O.Params(lat, omega, force=(F, 0.0))
+    y = np.arange(H)
+    ref = F / (2 * nu) * (y + 0.5) * (H - 0.5 - y)
+    rho = np.ones(mask.shape)
+    u = np.zeros((2,) + mask.shape)
+    u[0, 1:H + 1, :] = ref[:, None]          # start on the parabola
+    f = O.run(lat, O.init_state(lat, rho, u, mask, p), mask, p, steps)
+    _, uu = O.macroscopic(lat, f, mask, p)
+    return uu[0, 1:H + 1, 2], ref
+
+
+def test_poiseuille_exact_at_magic_tau():
+    """Force-driven channel between halfway bounce-back walls, BGK with
+    tau = 1/2 + sqrt(3/16): the lattice solution is the exact parabola
+    u(y) = F / (2 nu) (y + 1/2) (H - 1/2 - y) (zero wall slip at this tau is a
+    known property of BGK halfway bounce-back), when the reported velocity is
+    (j + F/2) / rho."""
+    got, ref = _poiseuille(8, 1.0 / (0.5 + np.sqrt(3.0 / 16.0)))
+    assert np.max(np.abs(got - ref)) < 1e-10 * ref.max()
+
+
+def test_poiseuille_profile_within_one_percent():
+    got, ref = _poiseuille(16, 1.0)
+    assert np.max(np.abs(got - ref)) < 0.01 * ref.max()
+
+
+def test_couette_moving_lid():
+    """Stationary bottom wall and moving top LID: linear profile
+    u_x(y) = U (y + 1/2) / H with the walls half a cell outside the fluid."""
+    lat = O.Lattice(9)
+    H = 16
+    U = 0.01
+    mask = I.channel_2d_mask(4, H + 2, top=O.LID)
+    p = O.Params(lat, 1.0, bc=O.BC(2, lid_u=(U, 0.0)))
+    rho = np.ones(mask.shape)
+    u = np.zeros((2,) + mask.shape)
+    f = O.run(lat, O.init_state(lat, rho, u, mask, p), mask, p, 6000)
+    _, uu = O.macroscopic(lat, f, mask, p)
+    y = np.arange(H)
+    ref = U * (y + 0.5) / H
+    np.testing.assert_allclose(uu[0, 1:H + 1, 1], ref, rtol=2e-3, atol=1e-6)
+
+
+def test_closed_box_conserves_mass():
+    lat = O.Lattice(19)
+    mask = I.lid_driven_cavity_mask(8)
+    mask[mask == O.LID] = O.WALL
+    mask |= I.random_obstacle_mask(mask.shape, 0.05, seed=2)
+    p = O.Params(lat, 1.5)
+    f = _perturbed_state(lat, mask.shape, seed=5)
+    f = O.init_state(lat, O.density(lat, f), O.momentum(lat, f) / O.density(lat, f), mask, p)
+    m0 = O.total_mass(lat, f, mask)
+    f = O.run(lat, f, mask, p, 200)
+    assert abs(O.total_mass(lat, f, mask) - m0) < 1e-12 * m0
+
+
+def test_zou_he_inlet_momentum_identity():
+    """At INLET cells the reconstructed populations give rho u_x = j_x and
+    rho = sum f exactly (the defining equations of the Zou-He density)."""
+    lat = O.Lattice(27)
+    mask = I.sphere_channel_mask(12, 6, 6, radius=1.5, center=(6, 3, 3))
+    uin = (0.04, 0.0, 0.0)
+    p = O.Params(lat, 1.6, collision="kbc", bc=O.BC(3, inlet_u=uin))
+    rho, u = I.random_flow(mask.shape, 3, seed=3, rho_amp=0.01, u_amp=0.02)
+    f = O.run(lat, O.init_state(lat, rho, u, mask, p), mask, p, 3)
+    sel = mask == O.INLET
+    r = O.density(lat, f)[sel]
+    jx = O.momentum(lat, f)[0][sel]
+    np.testing.assert_allclose(jx, r * uin[0], rtol=1e-13)
+
+
+def test_outflow_copies_left_neighbour():
+    lat = O.Lattice(9)
+    mask = np.zeros((5, 7), np.uint8)
+    mask[:, 0] = O.INLET
+    mask[:, 6] = O.OUTLET
+    rng = np.random.default_rng(1)
+    h = 1 / 9 + 0.01 * rng.standard_normal((9, 5, 7))
+    bc = O.BC(2, inlet_u=(0.03, 0.0))
+    fp = O.pull_plain(lat, h, mask, bc)
+    f = O.stream_bc(lat, h, mask, bc)
+    for i in range(9):
+        if lat.c[i, 0] == -1:
+            np.testing.assert_array_equal(f[i][:, 6], fp[i][:, 5])
+        else:
+            np.testing.assert_array_equal(f[i][:, 6], fp[i][:, 6])
+
+
+def test_stream_adjoint_is_inverse_permutation():
+    lat = O.Lattice(19)
+    g = np.random.default_rng(3).standard_normal((19, 3, 4, 5))
+    mask = np.zeros((3, 4, 5), np.uint8)
+    hb = O.stream_bc_vjp(lat, g, mask, O.BC(3))
+    for i in range(19):
+        np.testing.assert_array_equal(hb[i], lat.roll(g[i], i, sign=-1))
+        # inverse: applying the forward shift restores g
+        np.testing.assert_array_equal(lat.roll(hb[i], i), g[i])
+
+
+def test_stream_bc_adjoint_dot_product():
+    """<S_lin h, g> = <h, S^T g> with walls, moving lid and EQ cells (S_lin is
+    the linear part: the pull with the constant terms removed)."""
+    lat = O.Lattice(19)
+    shape = (5, 6, 7)
+    mask = I.random_obstacle_mask(shape, 0.15, seed=4)
+    mask[I.random_obstacle_mask(shape, 0.05, seed=5) > 0] = O.LID
+    mask[I.random_obstacle_mask(shape, 0.05, seed=6) > 0] = O.EQ
+    bc = O.BC(3, lid_u=(0.05, 0.01, 0.0), eq_rho=1.02, eq_u=(0.01, 0.0, 0.02))
+    rng = np.random.default_rng(8)
+    h = rng.standard_normal((19,) + shape)
+    g = rng.standard_normal((19,) + shape)
+    fl = O.fluid_like(mask)
+    lin = O.pull_plain(lat, h, mask, bc) - O.pull_plain(lat, 0 * h, mask, bc)
+    lhs = (np.where(fl[None], lin, 0) * g).sum()
+    rhs = (h * O.stream_bc_vjp(lat, g, mask, bc)).sum()
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+
+
+def _adjoint_case(q, shape, steps, with_walls, force):
+    lat = O.Lattice(q)
+    if with_walls:
+        mask = I.lid_driven_cavity_mask(shape[-1], *(shape[::-1][1:])) if lat.d == 3 else \
+            I.channel_2d_mask(shape[1], shape[0], top=O.LID)
+    else:
+        mask = np.zeros(shape, np.uint8)
+    bc = O.BC(lat.d, lid_u=(0.05,) + (0.0,) * (lat.d - 1))
+    p = O.Params(lat, 1.4, bc=bc, force=force)
+    rho0 = 1.0 + I.density_perturbation(shape, 1e-3, seed=21)
+    u0 = I.random_flow(shape, lat.d, seed=22, u_amp=0.02)[1]
+    box = tuple(slice(1, n - 1) for n in shape)
+
+    def loss(r0):
+        f = O.run(lat, O.init_state(lat, r0, u0, mask, p), mask, p, steps)
+        return O.kinetic_energy(lat, f, box)
+
+    def seed(fN):
+        return O.kinetic_energy_grads(lat, fN, box)
+
+    drho, _ = O.gradient_init(lat, rho0, u0, mask, p, steps, seed)
+    return lat, mask, rho0, loss, drho
+
+
+@pytest.mark.parametrize("q,shape,steps,walls,force", [
+    (9, (8, 9), 25, False, None),
+    (9, (9, 8), 25, True, (1e-4, 0.0)),
+    (19, (4, 5, 6), 10, False, None),
+    (19, (6, 6, 6), 8, True, None),
+])
+def test_adjoint_matches_complex_step(q, shape, steps, walls, force):
+    """The hand-derived adjoint gives the same directional derivative as the
+    complex-step method (no cancellation: agreement to ~1e-10)."""
+    lat, mask, rho0, loss, drho = _adjoint_case(q, shape, steps, walls, force)
+    fl = O.fluid_like(mask)
+    rng = np.random.default_rng(31)
+    h = 1e-30
+    for _ in range(3):
+        d = rng.standard_normal(shape) * fl
+        cs = np.imag(loss(rho0 + 1j * h * d)) / h
+        ad = float((drho * d).sum())
+        assert abs(ad - cs) <= 1e-9 * abs(cs)
+
+
+def test_adjoint_matches_central_fd():
+    lat, mask, rho0, loss, drho = _adjoint_case(19, (4, 5, 6), 10, False, None)
+    rng = np.random.default_rng(41)
+    eps = 1e-6
+    for _ in range(2):
+        d = rng.standard_normal(rho0.shape)
+        fd = (loss(rho0 + eps * d) - loss(rho0 - eps * d)) / (2 * eps)
+        assert abs(float((drho * d).sum()) - fd) <= 1e-6 * abs(fd)
