@@ -1,0 +1,422 @@
+"""Benchmark of the lattice Boltzmann hot path on one GB300 (or N replicas).
+
+Headline: MLUPS of the D3Q19 BGK lid-driven cavity on a 256^3 lattice, FP32
+storage, halfway bounce-back on five walls and a moving lid u = (0.05, 0, 0),
+Re = 1000 (nu = u L / Re with L = 254).  One benchmark step is one lattice
+update of all 256^3 cells (the paper's MLUPS counts every cell, collision +
+streaming + boundary conditions).  The populations (2 x 1.27 GB) are far larger
+than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extra]
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores instead (the paper ships no runnable reference here).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CAV = 256
+LID_U = 0.05
+RE = 1000.0
+BYTES_PER_CELL_F32 = 2 * 19 * 4   # one read + one write of 19 FP32 populations
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def cavity_omega(n=N_CAV):
+    nu = LID_U * (n - 2) / RE
+    return 1.0 / (3.0 * nu + 0.5)
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+def _cavity_sim(torch, X, I, n, storage, stream):
+    mask = I.lid_driven_cavity_mask(n)
+    sim = X.Simulation(19, (n, n, n), cavity_omega(n), "bgk", storage, stream=stream)
+    sim.set_mask(mask)
+    sim.set_bc(X.XLB_CELL_LID, 1.0, (LID_U, 0.0, 0.0))
+    sim.init()
+    return sim, mask
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_2311_16080_gb300 import inputs as I
+    from paper_2311_16080_gb300 import xlb as X
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    # a dedicated (non-default) stream: the library queues every kernel on it
+    # and the CUDA events below are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    assert stream.cuda_stream != 0
+    n = N_CAV
+    cells = n ** 3
+    sim, mask = _cavity_sim(torch, X, I, n, "f32", stream.cuda_stream)
+    fluid = int((mask == 0).sum())
+
+    # warm-up (also takes the one local collision after initialisation)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    mass, _ = sim.reduce()  # FP64 conservation check on every benchmark run
+    ms_step = ms_max / args.steps
+    mlups = world * cells * args.steps / (ms_max * 1e3)
+
+    # end to end through the public API with host buffers: upload mask and
+    # initial fields from pinned memory, K steps, read rho and u back.
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_mask = pin(mask)
+    h_rho = pin(np.ones(mask.shape, np.float32))
+    h_u = pin(np.zeros((3,) + mask.shape, np.float32))
+    o_rho = torch.empty(mask.shape, dtype=torch.float32).pin_memory()
+    o_u = torch.empty((3,) + mask.shape, dtype=torch.float32).pin_memory()
+    sim2 = X.Simulation(19, (n, n, n), cavity_omega(n), "bgk", "f32", stream=stream.cuda_stream)
+    sim2.set_bc(X.XLB_CELL_LID, 1.0, (LID_U, 0.0, 0.0))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim2.set_mask(h_mask)
+    sim2.init(h_rho, h_u)
+    sim2.step(args.steps)
+    X.xlb_macroscopic(sim2.ctx, o_rho, o_u)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    sim2.close()
+    e2e = {"value": world * cells * args.steps / (e2e_s * 1e6), "unit": "MLUPS",
+           "h2d_bytes_per_step": (h_mask.numel() + 4 * (h_rho.numel() + h_u.numel())) / args.steps,
+           "d2h_bytes_per_step": 4 * (o_rho.numel() + o_u.numel()) / args.steps}
+
+    peak, peak_kind = hbm_peak()
+    algo_bytes = BYTES_PER_CELL_F32 * fluid + cells  # populations of fluid cells + the mask byte
+    achieved = algo_bytes / (ms_step * 1e-3) / 1e9
+    if achieved > 1.15 * peak:
+        raise RuntimeError(f"timed kernel exceeds the measured copy bandwidth ({achieved:.0f} GB/s): "
+                           "the events do not bracket the work")
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+            "kernel": "k_stream_collide<19,float,BGK>",
+            "algorithmic_bytes_per_launch": algo_bytes,
+            "frac_of_8TBs_nominal": round(achieved / 8000.0, 4)}
+    prof_traffic = _profile_traffic()
+    if prof_traffic:
+        roof["traffic"] = prof_traffic
+
+    out = {"metric": "MLUPS", "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "D3Q19 BGK lid-driven cavity 256^3, FP32 storage, halfway bounce-back "
+                                  "walls + moving lid u=(0.05,0,0), Re=1000",
+                      "lattice": "D3Q19", "cells": cells, "fluid_cells": fluid, "omega": cavity_omega(n),
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                      "l2": "inputs larger than L2 (2.55 GB of populations per step), no flush"},
+           "e2e": e2e, "roofline": roof, "gpu_launches": args.steps,
+           "clocks": clk.summary(), "mass_fp64": mass}
+    sim.close()
+    torch.cuda.synchronize()
+    if rank == 0 and not args.no_extra:
+        out["extra"] = extras(args, torch, X, I, stream)
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
+    return out
+
+
+def _profile_traffic():
+    """DRAM bytes per launch of the stream-collide kernel from a committed ncu
+    summary (profiles/stream_collide_d3q19_cavity.txt), if present."""
+    p = os.path.join(ROOT, "profiles", "stream_collide_d3q19_cavity.txt")
+    try:
+        for line in open(p):
+            if line.startswith("traffic_bytes_per_launch_256cube:"):
+                return float(line.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+def extras(args, torch, X, I, stream):
+    """Secondary figures of the metric: low-precision storage MLUPS and error,
+    KBC D3Q27 MLUPS, adjoint MLUPS (kernel and end-to-end)."""
+    res = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(sim, k):
+        a, b = ev(), ev()
+        a.record(stream)
+        sim.step(k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    n = N_CAV
+    for st in ("f16", "bf16"):
+        sim, _ = _cavity_sim(torch, X, I, n, st, stream.cuda_stream)
+        sim.step(10)
+        ms = timed(sim, 300)
+        res[f"cavity256_{st}_mlups"] = round(n ** 3 / (ms * 1e3), 1)
+        res[f"cavity256_{st}_algo_GBs"] = round(2 * 19 * 2 * n ** 3 / (ms * 1e-3) / 1e9, 1)
+        sim.close()
+
+    # KBC D3Q27 flow past a sphere, 512 x 256 x 256, Zou-He inlet + outflow
+    mask = I.sphere_channel_mask(512, 256, 256, radius=32, center=(128, 128, 128))
+    for st in ("f32", "f16"):
+        sim = X.Simulation(27, (512, 256, 256), 1.857, "kbc", st, stream=stream.cuda_stream)
+        sim.set_mask(mask)
+        sim.set_bc(X.XLB_CELL_INLET, 1.0, (0.04, 0.0, 0.0))
+        sim.init()
+        sim.step(5)
+        ms = timed(sim, 50)
+        cells = 512 * 256 * 256
+        res[f"kbc_d3q27_sphere_{st}_mlups"] = round(cells / (ms * 1e3), 1)
+        res[f"kbc_d3q27_sphere_{st}_algo_GBs"] = round(2 * 27 * (4 if st == "f32" else 2) * cells / (ms * 1e-3) / 1e9, 1)
+        sim.close()
+    del mask
+
+    # adjoint: D3Q19 128^3 periodic, 500 steps, checkpoints every 50
+    m = 128
+    rho0 = (1.0 + I.density_perturbation((m, m, m), 1e-3, seed=1234)).astype(np.float32)
+    sim = X.Simulation(19, (m, m, m), 1.25, "bgk", "f32", stream=stream.cuda_stream)
+    sim.init(rho0, None)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X.xlb_tape_begin(sim.ctx, 500, 50)
+    sim.step(500)
+    rho = torch.empty((m, m, m), dtype=torch.float32, device="cuda")
+    u = torch.empty((3, m, m, m), dtype=torch.float32, device="cuda")
+    X.xlb_macroscopic(sim.ctx, rho, u)
+    box = (slice(48, 80),) * 3
+    rb = torch.zeros_like(rho)
+    ub = torch.zeros_like(u)
+    rb[box] = 0.5 * (u[(slice(None),) + box] ** 2).sum(0)
+    ub[(slice(None),) + box] = rho[box] * u[(slice(None),) + box]
+    X.xlb_adjoint_seed_macro(sim.ctx, rb, ub)
+    X.xlb_profile_enable(sim.ctx, True)
+    X.xlb_adjoint_step(sim.ctx, 500)
+    g = torch.empty((m, m, m), dtype=torch.float32, device="cuda")
+    X.xlb_adjoint_init_grad(sim.ctx, g, None)
+    torch.cuda.synchronize()
+    grad_s = time.perf_counter() - t0
+    adj_ms, adj_n = X.xlb_profile_read(sim.ctx, 1)
+    X.xlb_tape_end(sim.ctx)
+    sim.close()
+    cells = m ** 3
+    if adj_n:
+        per = adj_ms / adj_n
+        res["adjoint_d3q19_128_kernel_mlups"] = round(cells / (per * 1e3), 1)
+        res["adjoint_d3q19_128_kernel_algo_GBs"] = round(228 * cells / (per * 1e-3) / 1e9, 1)
+    res["adjoint_d3q19_128_gradient_e2e_s"] = round(grad_s, 4)
+    res["adjoint_d3q19_128_gradient_e2e_mlups"] = round(500 * cells / (grad_s * 1e6), 1)
+    res["adjoint_grad_norm"] = float(torch.linalg.vector_norm(g.double()).item())
+
+    # storage error: Taylor-Green 128^2, 1000 steps, against the FP64 oracle
+    try:
+        from oracle import lbm as O
+        nt = 128
+        r0, u0 = I.taylor_green_2d(nt, nt, 0.04)
+        lat = O.Lattice(9)
+        msk = np.zeros((nt, nt), np.uint8)
+        p = O.Params(lat, 1.25)
+        f = O.run(lat, O.init_state(lat, r0, u0, msk, p), msk, p, 1000)
+        _, uo = O.macroscopic(lat, f, msk, p)
+        for st in ("f32", "f16", "bf16"):
+            s = X.Simulation(9, (nt, nt), 1.25, "bgk", st, stream=stream.cuda_stream)
+            s.init(r0.astype(np.float32), u0.astype(np.float32))
+            s.step(1000)
+            _, ug = s.macroscopic()
+            s.close()
+            err = float(np.sqrt(((ug - uo) ** 2).sum() / (uo ** 2).sum()))
+            res[f"tg128_{st}_store_rel_l2_u"] = err
+    except Exception as e:  # the error figures are secondary; keep the line
+        res["tg128_error"] = repr(e)
+    return res
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+
+def _oracle_cavity_steps(n, steps_or_seconds, by_time):
+    from oracle import lbm as O
+    from paper_2311_16080_gb300 import inputs as I
+    lat = O.Lattice(19)
+    mask = I.lid_driven_cavity_mask(n)
+    p = O.Params(lat, cavity_omega(N_CAV), bc=O.BC(3, lid_u=(LID_U, 0.0, 0.0)))
+    f = O.init_state(lat, np.ones(mask.shape), np.zeros((3,) + mask.shape), mask, p)
+    f = O.step(lat, f, mask, p)
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        f = O.step(lat, f, mask, p)
+        done += 1
+        el = time.perf_counter() - t0
+        if (by_time and el >= steps_or_seconds) or (not by_time and done >= steps_or_seconds):
+            break
+    return done, el
+
+
+def cpu_baseline(seconds=15.0, n=48):
+    """Oracle timed on the host on a bounded sample of the workload, in a
+    single-threaded child process (numpy / BLAS pinned to one thread)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench, json; "
+            f"d, el = bench._oracle_cavity_steps({n}, {seconds}, True); print(json.dumps([d, el]))")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=seconds * 6 + 120)
+        done, el = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:
+        return {"value": None, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": f"failed: {e!r}"}
+    return {"value": round(n ** 3 * done / (el * 1e6), 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{n}^3 lid-driven cavity (same mask recipe, omega and lid), {done} steps, {el:.1f} s, "
+                      "FP64 numpy oracle, one thread"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    n = 32
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench, json; "
+            f"bench._oracle_cavity_steps({n}, {args.warmup}, False); "
+            f"d, el = bench._oracle_cavity_steps({n}, {args.steps}, False); print(json.dumps([d, el]))")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True)
+    done, el = json.loads(r.stdout.strip().splitlines()[-1])
+    v = n ** 3 * done / (el * 1e6)
+    return {"impl": "reference", "metric": "MLUPS", "value": round(v, 4), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / done, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "D3Q19 BGK lid-driven cavity 256^3, FP32 storage, halfway bounce-back "
+                                   "walls + moving lid u=(0.05,0,0), Re=1000",
+                       "sample": f"{n}^3 crop of the same recipe per step"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{n}^3 lid-driven cavity per step, FP64 numpy oracle, one thread"},
+            "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            dist.init_process_group("nccl")
+        out = run_ours(args, rank, world, dist)
+        if dist:
+            dist.destroy_process_group()
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

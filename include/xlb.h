@@ -1,0 +1,198 @@
+/*
+ * xlb.h - C ABI of the GB300 lattice Boltzmann hot path (libxlb.so).
+ *
+ * The library advances a lattice Boltzmann simulation on one GPU: the fused
+ * stream-and-collide update of Section 2 (Eqs. 1-2; BGK Eq. 3 with the
+ * equilibrium of Eq. 5, or the KBC entropic collision Section 2 names), the
+ * mask-driven boundary conditions of Section 3.5, the mixed storage precision
+ * of Section 3.7, reverse-mode differentiation of the step (Section 3.6) and a
+ * batched launch over many small 2D domains (the vmap batching of Section 6).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an xlb_status; nothing aborts the process.
+ *    xlb_last_error() gives a one-line reason for the last failure on a ctx.
+ *  - Lattice fields are x-fastest: cell (x, y, z) sits at x + nx*(y + ny*z).
+ *    Vector fields are component-major: u[a*N + cell], a = x, y (, z).
+ *  - Pointers passed in may be host or device memory (the library asks CUDA
+ *    which).  They are borrowed for the duration of the call only.
+ *  - Work is queued on the ctx's stream.  Calls that read results into host
+ *    memory synchronise that stream before returning; the others are
+ *    asynchronous.
+ *  - The library owns every population, mask, tape and scratch buffer.
+ *  - Populations are stored as deviations f_i - w_i (rho0 = 1) in the chosen
+ *    storage type; all arithmetic is FP32, global sums are FP64.
+ */
+#ifndef XLB_H
+#define XLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct xlb_ctx xlb_ctx;
+
+typedef enum {
+  XLB_OK = 0,
+  XLB_ERR_ARG = 1,         /* invalid argument (null, size, code out of range)      */
+  XLB_ERR_UNSUPPORTED = 2, /* valid but not provided (e.g. KBC on D3Q19)           */
+  XLB_ERR_OOM = 3,         /* device allocation failed                              */
+  XLB_ERR_CUDA = 4,        /* a CUDA call failed; xlb_last_error has its message   */
+  XLB_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired                    */
+  XLB_ERR_STATE = 6        /* call out of order (e.g. adjoint before a tape)       */
+} xlb_status;
+
+/* Lattices of Figure 1 (Section 3.2): the value is Q. */
+enum { XLB_D2Q9 = 9, XLB_D3Q19 = 19, XLB_D3Q27 = 27 };
+
+/* Collision models (Section 2): NONE streams only (a pure permutation). */
+enum { XLB_COLL_NONE = 0, XLB_COLL_BGK = 1, XLB_COLL_KBC = 2 };
+
+/* Storage precision of populations (Section 3.7 "compute/storage"): the
+ * compute type is always FP32.  F16/BF16 store shifted populations
+ * f_i - w_i rounded to nearest even (the centring Section 4.1 cites). */
+enum { XLB_STORE_F32 = 0, XLB_STORE_F16 = 1, XLB_STORE_BF16 = 2 };
+
+/* Cell types of the mask (Section 3.5).  For a fluid-like cell x and a
+ * direction i whose source cell x - c_i is
+ *   FLUID/INLET/OUTLET: f_i(x) = h_i(x - c_i)                 (Eq. 2, periodic)
+ *   WALL:   f_i(x) = h_opp(i)(x)                                (halfway bounce-back)
+ *   LID:    f_i(x) = h_opp(i)(x) + 2 w_i rho_w (c_i . u_w) / cs^2 (moving wall)
+ *   EQ:     f_i(x) = f_i^eq(rho_w, u_w)                         (equilibrium BC)
+ * where h is the post-collision state.  INLET cells then rebuild their c_x=+1
+ * populations by Zou-He for the inlet velocity; OUTLET cells copy their
+ * c_x=-1 populations from the cell at x-1 (zero-gradient outflow). */
+enum {
+  XLB_CELL_FLUID = 0,
+  XLB_CELL_WALL = 1,
+  XLB_CELL_LID = 2,
+  XLB_CELL_INLET = 3,
+  XLB_CELL_OUTLET = 4,
+  XLB_CELL_EQ = 5
+};
+
+/* ---- simulation context ------------------------------------------------ */
+
+/* Create a simulation of nx*ny*nz cells (dims = {nx, ny, nz}; nz = 1 for
+ * D2Q9) with relaxation rate omega = dt/tau (Eq. 3; tau from Eq. 4).
+ * collision: XLB_COLL_*; KBC is defined on D2Q9 and D3Q27 only
+ * (XLB_ERR_UNSUPPORTED on D3Q19).  storage: XLB_STORE_*.  cuda_stream: a
+ * cudaStream_t to queue work on, or NULL for a stream the library creates.
+ * Every face is periodic until a mask is set.  Allocates two population
+ * buffers of Q*N elements.  On failure *out is NULL. */
+int xlb_create(xlb_ctx** out, int lattice, const int64_t dims[3], double omega, int collision, int storage,
+               void* cuda_stream);
+
+/* Release every buffer of the ctx (NULL is accepted). */
+void xlb_destroy(xlb_ctx* ctx);
+
+/* One-line description of the last failure on ctx ("" if none); valid until
+ * the next call on ctx.  ctx may be NULL (reports creation failures). */
+const char* xlb_last_error(const xlb_ctx* ctx);
+
+/* Static name of a status code. */
+const char* xlb_status_string(int status);
+
+/* omega = 1 / (nu / cs^2 + 1/2) with dt = 1 (Eq. 4). */
+double xlb_omega_from_nu(double nu);
+
+/* Set the per-cell type mask (uint8 codes XLB_CELL_*, N cells, x fastest).
+ * Codes >= 6 give XLB_ERR_ARG and leave the previous mask in place. */
+int xlb_set_mask(xlb_ctx* ctx, const uint8_t* mask);
+
+/* Prescribed state of a boundary type: XLB_CELL_LID (rho_w, u_w of the
+ * moving wall), XLB_CELL_INLET (Zou-He velocity u; rho ignored) or
+ * XLB_CELL_EQ (rho_w, u_w of the equilibrium BC).  u has 3 components (the
+ * third is ignored on D2Q9).  Default: rho = 1, u = 0. */
+int xlb_set_bc(xlb_ctx* ctx, int cell_type, float rho, const float u[3]);
+
+/* Constant body force F (3 components) on fluid-like cells, applied by the
+ * exact-difference method (Section 6.1): f* += f^eq(rho, u + F/rho) - f^eq(rho, u).
+ * The reported velocity becomes (j + F/2) / rho. */
+int xlb_set_force(xlb_ctx* ctx, const float F[3]);
+
+/* f_0 = f^eq(rho, u) (Eq. 5) on fluid-like cells, boundary values elsewhere;
+ * resets the step counter to 0.  rho: N values or NULL (rho = 1); u: D*N
+ * values, component-major, or NULL (u = 0).  The fields are kept on the
+ * device for xlb_adjoint_init_grad. */
+int xlb_init(xlb_ctx* ctx, const float* rho, const float* u);
+
+/* Advance n >= 0 time steps: f_{t+1} = S_bc(C(f_t)) (Eqs. 1-2, Section 3.6).
+ * Asynchronous.  While a tape is open (xlb_tape_begin) the checkpoints of the
+ * tape are recorded and stepping past its length is XLB_ERR_STATE. */
+int xlb_step(xlb_ctx* ctx, int64_t n);
+
+/* Number of steps taken since xlb_init / xlb_state_set. */
+int xlb_get_time(const xlb_ctx* ctx, int64_t* t);
+
+/* rho (N values) and u (D*N, component-major) of the current post-stream
+ * state (Eqs. 6-7).  Either pointer may be NULL.  Solid cells report zeros;
+ * EQ cells report their prescribed state. */
+int xlb_macroscopic(xlb_ctx* ctx, float* rho, float* u);
+
+/* FP64 totals over fluid-like cells of the current post-stream state:
+ * out_mass[0] = sum rho, out_mom[0..2] = sum j (bare momentum, no force
+ * shift).  Host outputs; synchronises. */
+int xlb_reduce(xlb_ctx* ctx, double out_mass[1], double out_mom[3]);
+
+/* Wait for all work queued on the ctx's stream. */
+int xlb_synchronize(xlb_ctx* ctx);
+
+/* ---- checkpoint / resume (Section 3.7) --------------------------------- */
+
+/* Size in bytes of a serialized state (header + populations). */
+int xlb_state_bytes(const xlb_ctx* ctx, size_t* bytes);
+
+/* Serialize the state (step counter, whether it holds pre- or
+ * post-collision populations, raw stored deviations) into buf (host or
+ * device, at least xlb_state_bytes).  Synchronises. */
+int xlb_state_get(xlb_ctx* ctx, void* buf, size_t bytes);
+
+/* Restore a state written by xlb_state_get of a ctx with the same lattice,
+ * dims and storage (XLB_ERR_ARG otherwise). */
+int xlb_state_set(xlb_ctx* ctx, const void* buf, size_t bytes);
+
+/* Device pointer and element stride of the live population buffer (for
+ * zero-copy inspection; valid until the next xlb_step). */
+int xlb_populations(xlb_ctx* ctx, void** dev_ptr, int64_t* plane_stride);
+
+/* ---- reverse mode (Section 3.6 grad of step; Section 7 adjoint) -------- */
+
+/* Open a tape right after xlb_init: the next xlb_step calls (n_steps in
+ * total) record a checkpoint every checkpoint_every steps.  The adjoint then
+ * recomputes each segment from its checkpoint.  BGK or NONE collision; masks
+ * with INLET / OUTLET cells are XLB_ERR_UNSUPPORTED. */
+int xlb_tape_begin(xlb_ctx* ctx, int64_t n_steps, int64_t checkpoint_every);
+
+/* Seed the adjoint at the final step with the loss cotangents of the
+ * observables xlb_macroscopic returns: dL_drho (N) and dL_du (D*N); either
+ * may be NULL (zero).  Requires all n_steps of the tape to have been taken. */
+int xlb_adjoint_seed_macro(xlb_ctx* ctx, const float* dL_drho, const float* dL_du);
+
+/* Propagate the adjoint n steps backwards (n <= steps remaining). */
+int xlb_adjoint_step(xlb_ctx* ctx, int64_t n);
+
+/* After the adjoint reached step 0: gradients of the loss with respect to
+ * the initial fields given to xlb_init, dL_drho0 (N) and dL_du0 (D*N); either
+ * may be NULL.  Solid and EQ cells get 0. */
+int xlb_adjoint_init_grad(xlb_ctx* ctx, float* dL_drho0, float* dL_du0);
+
+/* Free the tape, checkpoints and adjoint buffers. */
+int xlb_tape_end(xlb_ctx* ctx);
+
+/* ---- timing of the hot kernels ----------------------------------------- */
+
+/* Total device time in ms of the launches of one kernel class recorded
+ * since the last reset, measured with CUDA events on the ctx's stream, and
+ * the number of launches.  kernel: 0 = fused stream-collide, 1 = adjoint step.
+ * Enable with xlb_profile_enable(ctx, 1) (adds two event records per launch). */
+int xlb_profile_enable(xlb_ctx* ctx, int on);
+int xlb_profile_read(xlb_ctx* ctx, int kernel, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XLB_H */

@@ -484,47 +484,49 @@ def collide_vjp(lat: Lattice, f, mask, p: Params, hbar):
     return np.where(fl[None], fb, hbar)
 
 
-def macroscopic_seed(lat: Lattice, f, rbar, ubar):
-    """dL/df of a loss given through dL/drho and dL/du of the bare moments
-    rho = sum f, u = j / rho:  fbar_i = rbar + ubar . (c_i - u) / rho."""
-    rho = density(lat, f)
-    u = momentum(lat, f) / rho
+def macroscopic_seed(lat: Lattice, f, mask, p: Params, rbar, ubar):
+    """dL/df of a loss given through the cotangents (rbar, ubar) of the
+    reported observables rho = sum f, u = (j + F/2) / rho:
+    fbar_i = rbar + ubar . (c_i - u) / rho on fluid-like cells, 0 elsewhere."""
+    rho, u = macroscopic(lat, f, mask, p)
+    fl = fluid_like(mask)
+    safe = np.where(fl, rho, 1.0)
     out = []
     for i in range(lat.q):
-        out.append(rbar + sum(ubar[a] * (lat.c[i, a] - u[a]) for a in range(lat.d)) / rho)
+        v = rbar + sum(ubar[a] * (lat.c[i, a] - u[a]) for a in range(lat.d)) / safe
+        out.append(np.where(fl, v, 0.0))
     return np.stack(out)
 
 
-def kinetic_energy(lat: Lattice, f, box):
-    """L = sum over the box of (1/2) rho |u|^2 = (1/2) |j|^2 / rho (complex-safe)."""
-    rho = density(lat, f)
-    j = momentum(lat, f)
-    ke = 0.5 * sum(j[a] * j[a] for a in range(lat.d)) / rho
+def kinetic_energy(lat: Lattice, f, mask, p: Params, box):
+    """L = sum over the box of (1/2) rho |u|^2 of the reported observables
+    (complex-safe: no absolute values)."""
+    rho, u = macroscopic(lat, f, mask, p)
+    ke = 0.5 * rho * sum(u[a] * u[a] for a in range(lat.d))
     return ke[box].sum()
 
 
-def kinetic_energy_grads(lat: Lattice, f, box):
-    """(dL/drho, dL/du) of ``kinetic_energy`` with u = j / rho treated as the
-    independent variable: L = (1/2) rho |u|^2 on the box."""
-    rho = density(lat, f)
-    u = momentum(lat, f) / rho
+def kinetic_energy_grads(rho, u, box):
+    """(dL/drho, dL/du) of ``kinetic_energy``: (1/2)|u|^2 and rho u on the box."""
     inb = np.zeros(rho.shape, dtype=bool)
     inb[box] = True
-    rbar = np.where(inb, 0.5 * sum(u[a] * u[a] for a in range(lat.d)), 0.0)
-    ubar = np.stack([np.where(inb, rho * u[a], 0.0) for a in range(lat.d)])
+    rbar = np.where(inb, 0.5 * sum(u[a] * u[a] for a in range(u.shape[0])), 0.0)
+    ubar = np.stack([np.where(inb, rho * u[a], 0.0) for a in range(u.shape[0])])
     return rbar, ubar
 
 
 def gradient_init(lat: Lattice, rho0, u0, mask, p: Params, n, seed_fn):
     """Reverse-mode gradient of L(f_n) with respect to the initial fields of
     f_0 = f^eq(rho0, u0): stores every f_t, then runs the adjoint backwards.
-    ``seed_fn(f_n) -> (dL/drho, dL/du)`` gives the loss cotangent.
+    ``seed_fn(rho_n, u_n) -> (dL/drho, dL/du)`` gives the loss cotangents of
+    the reported observables of f_n.
     Returns (dL/drho0, dL/du0) on fluid-like cells."""
     fs = [init_state(lat, rho0, u0, mask, p)]
     for _ in range(n):
         fs.append(step(lat, fs[-1], mask, p))
-    rb, ub = seed_fn(fs[-1])
-    fbar = macroscopic_seed(lat, fs[-1], rb, ub)
+    rho_n, u_n = macroscopic(lat, fs[-1], mask, p)
+    rb, ub = seed_fn(rho_n, u_n)
+    fbar = macroscopic_seed(lat, fs[-1], mask, p, rb, ub)
     for t in range(n - 1, -1, -1):
         hbar = stream_bc_vjp(lat, fbar, mask, p.bc)
         fbar = collide_vjp(lat, fs[t], mask, p, hbar)

@@ -1,0 +1,829 @@
+// Host implementation of the C ABI declared in include/xlb.h.
+//
+// State machine of a ctx:
+//  - xlb_init writes f_0 (post-stream populations) and marks the buffer as
+//    "pre-collision" (kind_h = 0).  The first step after that is a local
+//    collision (h_0 = C(f_0)); every later step is one fused stream-collide
+//    launch h_t = C(S_bc(h_{t-1})).  The stored buffer after t steps is
+//    h_{t-1}, and the observables of f_t = S_bc(h_{t-1}) are computed by a pull
+//    inside the readout kernels.  (S_bc C)^n = S_bc (C S_bc)^(n-1) C, so this is
+//    the same sequence of operations as Eqs. 1-2 applied n times.
+//  - A tape records h_{sk-1} at every time sk < T; the adjoint recomputes one
+//    segment of k states from its checkpoint before walking it backwards.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/xlb.h"
+#include "adjoint.h"
+#include "launch.h"
+#include "lattice.cuh"
+
+using namespace xlb;
+
+struct EventPair {
+  cudaEvent_t a, b;
+};
+
+struct xlb_ctx {
+  int Q = 0, D = 0, coll = 0, storage = 0, esize = 4;
+  int64_t nx = 0, ny = 0, nz = 0;
+  long long N = 0, plane = 0;
+  double omega = 1.0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint8_t* flags = nullptr;
+  bool has_mask = false;
+  bool has_inlet_outlet = false;
+  float* init_fields = nullptr;  // (1 + D) * N: rho0, u0 (component-major)
+  bool has_init = false;
+  int kind_h = 0;
+  int64_t t = 0;
+  // boundary values and force
+  float lid_rho = 1.f, lid_u[3] = {0, 0, 0};
+  float inlet_u[3] = {0, 0, 0};
+  float eq_rho = 1.f, eq_u[3] = {0, 0, 0};
+  float F[3] = {0, 0, 0};
+  bool has_force = false;
+  // scratch
+  double* partial = nullptr;
+  long long partial_cap = 0;
+  double* red_out = nullptr;
+  int* err_word = nullptr;
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  // tape / adjoint
+  bool tape_open = false;
+  int64_t tape_T = 0, tape_k = 0;
+  std::vector<void*> ckpt;
+  std::vector<void*> slots;
+  int64_t seg_loaded = -1;
+  float* abar[2] = {nullptr, nullptr};
+  int acur = 0;
+  int64_t adj_t = -1;  // time index of the adjoint held in abar[acur]
+  // profiling
+  bool prof = false;
+  std::vector<EventPair> ev_pool;
+  std::vector<int> ev_kind;
+  size_t ev_used = 0;
+  std::string err;
+};
+
+static std::string g_create_err;
+
+static int fail(xlb_ctx* c, int code, const char* fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof msg, fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = msg;
+  else
+    g_create_err = msg;
+  return code;
+}
+
+static int cuda_fail(xlb_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? XLB_ERR_OOM : XLB_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define CK(call)                                           \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+  } while (0)
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static size_t state_elems(const xlb_ctx* c) { return (size_t)c->Q * (size_t)c->plane; }
+static size_t state_bytes_raw(const xlb_ctx* c) { return state_elems(c) * (size_t)c->esize; }
+
+static int ensure_stage(xlb_ctx* c, size_t bytes) {
+  if (c->stage_bytes >= bytes) return XLB_OK;
+  if (c->stage) cudaFree(c->stage);
+  c->stage = nullptr;
+  c->stage_bytes = 0;
+  CK(cudaMalloc(&c->stage, bytes));
+  c->stage_bytes = bytes;
+  return XLB_OK;
+}
+
+static StepParams make_params(const xlb_ctx* c) {
+  StepParams p;
+  memset(&p, 0, sizeof p);
+  p.nx = (int)c->nx;
+  p.ny = (int)c->ny;
+  p.nz = (int)c->nz;
+  p.plane = c->plane;
+  p.omega = (float)c->omega;
+  p.has_mask = c->has_mask ? 1 : 0;
+  p.flags = c->flags;
+  p.has_force = c->has_force ? 1 : 0;
+  for (int a = 0; a < 3; ++a) {
+    p.F[a] = c->F[a];
+    p.eq_u[a] = c->eq_u[a];
+    p.inlet_u[a] = c->inlet_u[a];
+  }
+  if (c->D == 2) {
+    p.F[2] = 0.f;
+    p.eq_u[2] = 0.f;
+    p.inlet_u[2] = 0.f;
+  }
+  p.eq_rho = c->eq_rho;
+  // constant boundary terms per direction, in double then rounded once
+  auto fill = [&](auto lat_tag) {
+    constexpr int Q = decltype(lat_tag)::value;
+    const double eu[3] = {c->eq_u[0], c->eq_u[1], Lattice<Q>::D == 3 ? c->eq_u[2] : 0.0};
+    const double lu[3] = {c->lid_u[0], c->lid_u[1], Lattice<Q>::D == 3 ? c->lid_u[2] : 0.0};
+    const double usq = eu[0] * eu[0] + eu[1] * eu[1] + eu[2] * eu[2];
+    for (int i = 0; i < Q; ++i) {
+      const double w = weight_d<Q>(i);
+      const double cu = Lattice<Q>::c(i, 0) * eu[0] + Lattice<Q>::c(i, 1) * eu[1] + Lattice<Q>::c(i, 2) * eu[2];
+      p.eq_df[i] = (float)(w * (c->eq_rho - 1.0) + w * c->eq_rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
+      const double cl = Lattice<Q>::c(i, 0) * lu[0] + Lattice<Q>::c(i, 1) * lu[1] + Lattice<Q>::c(i, 2) * lu[2];
+      p.lid_term[i] = (float)(6.0 * w * c->lid_rho * cl);
+    }
+  };
+  if (c->Q == 9) fill(std::integral_constant<int, 9>());
+  if (c->Q == 19) fill(std::integral_constant<int, 19>());
+  if (c->Q == 27) fill(std::integral_constant<int, 27>());
+  return p;
+}
+
+static int dispatch(xlb_ctx* c, Op op, const LaunchArgs& a) {
+  int r;
+  if (c->Q == 9)
+    r = launch_d2q9(op, a);
+  else if (c->Q == 19)
+    r = launch_d3q19(op, a);
+  else
+    r = launch_d3q27(op, a);
+  if (r != 0) return fail(c, XLB_ERR_UNSUPPORTED, "launch of op %d rejected (code %d)", (int)op, r);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  return XLB_OK;
+}
+
+static LaunchArgs base_args(xlb_ctx* c) {
+  LaunchArgs a;
+  memset(&a, 0, sizeof a);
+  a.p = make_params(c);
+  a.storage = c->storage;
+  a.coll = c->coll;
+  a.ucs = c->N;
+  a.stream = c->stream;
+  a.partial = c->partial;
+  a.partial_capacity = c->partial_cap;
+  return a;
+}
+
+static cudaEvent_t* prof_begin(xlb_ctx* c, int kind) {
+  if (!c->prof) return nullptr;
+  if (c->ev_used == c->ev_pool.size()) {
+    EventPair e;
+    if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) return nullptr;
+    c->ev_pool.push_back(e);
+    c->ev_kind.push_back(kind);
+  }
+  c->ev_kind[c->ev_used] = kind;
+  EventPair& e = c->ev_pool[c->ev_used++];
+  cudaEventRecord(e.a, c->stream);
+  return &e.b;
+}
+
+static void prof_end(xlb_ctx* c, cudaEvent_t* b) {
+  if (b) cudaEventRecord(*b, c->stream);
+}
+
+// One fused step from buffer src to dst (either the live pair or tape slots).
+static int launch_step(xlb_ctx* c, const void* src, void* dst) {
+  LaunchArgs a = base_args(c);
+  a.src = src;
+  a.dst = dst;
+  cudaEvent_t* pe = prof_begin(c, 0);
+  int r = dispatch(c, OP_STEP, a);
+  prof_end(c, pe);
+  return r;
+}
+
+static int launch_collide_local(xlb_ctx* c, void* buf) {
+  LaunchArgs a = base_args(c);
+  a.dst = buf;
+  return dispatch(c, OP_COLLIDE_LOCAL, a);
+}
+
+static int launch_init(xlb_ctx* c, void* dst) {
+  LaunchArgs a = base_args(c);
+  a.dst = dst;
+  a.rho = c->init_fields;
+  a.u = c->init_fields + c->N;
+  return dispatch(c, OP_INIT, a);
+}
+
+extern "C" {
+
+const char* xlb_status_string(int s) {
+  switch (s) {
+    case XLB_OK: return "XLB_OK";
+    case XLB_ERR_ARG: return "XLB_ERR_ARG";
+    case XLB_ERR_UNSUPPORTED: return "XLB_ERR_UNSUPPORTED";
+    case XLB_ERR_OOM: return "XLB_ERR_OOM";
+    case XLB_ERR_CUDA: return "XLB_ERR_CUDA";
+    case XLB_ERR_TIMEOUT: return "XLB_ERR_TIMEOUT";
+    case XLB_ERR_STATE: return "XLB_ERR_STATE";
+    default: return "XLB_ERR_UNKNOWN";
+  }
+}
+
+const char* xlb_last_error(const xlb_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+double xlb_omega_from_nu(double nu) { return 1.0 / (3.0 * nu + 0.5); }
+
+int xlb_create(xlb_ctx** out, int lattice, const int64_t dims[3], double omega, int collision, int storage,
+               void* cuda_stream) {
+  if (!out) return fail(nullptr, XLB_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (lattice != 9 && lattice != 19 && lattice != 27) return fail(nullptr, XLB_ERR_ARG, "lattice must be 9, 19 or 27");
+  if (!dims) return fail(nullptr, XLB_ERR_ARG, "dims is null");
+  const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+  if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, XLB_ERR_ARG, "dims must be >= 1");
+  if (lattice == 9 && nz != 1) return fail(nullptr, XLB_ERR_ARG, "D2Q9 needs nz = 1");
+  if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30) || nx * ny > (1LL << 40) || nx * ny * nz > (1LL << 40))
+    return fail(nullptr, XLB_ERR_ARG, "dims too large");
+  if (!(omega > 0.0 && omega < 2.0)) return fail(nullptr, XLB_ERR_ARG, "omega must lie in (0, 2)");
+  if (collision < 0 || collision > 2) return fail(nullptr, XLB_ERR_ARG, "unknown collision %d", collision);
+  if (collision == XLB_COLL_KBC && lattice == 19)
+    return fail(nullptr, XLB_ERR_UNSUPPORTED, "KBC is defined on D2Q9 and D3Q27 only");
+  if (storage < 0 || storage > 2) return fail(nullptr, XLB_ERR_ARG, "unknown storage %d", storage);
+
+  xlb_ctx* c = new xlb_ctx();
+  c->Q = lattice;
+  c->D = lattice == 9 ? 2 : 3;
+  c->coll = collision;
+  c->storage = storage;
+  c->esize = storage == XLB_STORE_F32 ? 4 : 2;
+  c->nx = nx;
+  c->ny = ny;
+  c->nz = nz;
+  c->N = nx * ny * nz;
+  // population planes start on 256-byte boundaries
+  const long long align = 256 / c->esize;
+  c->plane = (c->N + align - 1) / align * align;
+  c->omega = omega;
+  auto bail = [&](int code) {
+    g_create_err = c->err;
+    xlb_destroy(c);
+    return code;
+  };
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaGetDevice"));
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamCreate"));
+    c->own_stream = true;
+  }
+  for (int k = 0; k < 2; ++k) {
+    e = cudaMalloc(&c->buf[k], state_bytes_raw(c));
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(populations)"));
+  }
+  StepParams p = make_params(c);
+  c->partial_cap = row_blocks(p);
+  e = cudaMalloc(&c->partial, sizeof(double) * 4 * (size_t)(c->partial_cap > 0 ? c->partial_cap : 1));
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(partials)"));
+  e = cudaMalloc(&c->red_out, 4 * sizeof(double) + sizeof(int) * 4);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(reduction)"));
+  c->err_word = (int*)(c->red_out + 4);
+  e = cudaMalloc(&c->init_fields, sizeof(float) * (size_t)(1 + c->D) * (size_t)c->N);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(init fields)"));
+  *out = c;
+  return XLB_OK;
+}
+
+int xlb_tape_end(xlb_ctx* c);
+
+void xlb_destroy(xlb_ctx* c) {
+  if (!c) return;
+  xlb_tape_end(c);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (int k = 0; k < 2; ++k)
+    if (c->buf[k]) cudaFree(c->buf[k]);
+  if (c->flags) cudaFree(c->flags);
+  if (c->init_fields) cudaFree(c->init_fields);
+  if (c->partial) cudaFree(c->partial);
+  if (c->red_out) cudaFree(c->red_out);
+  if (c->stage) cudaFree(c->stage);
+  for (auto& e : c->ev_pool) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
+  if (!c) return XLB_ERR_ARG;
+  if (!mask) return fail(c, XLB_ERR_ARG, "mask is null");
+  const size_t n = (size_t)c->N;
+  uint8_t* dmask = nullptr;
+  bool host_mask = !is_device_ptr(mask);
+  if (host_mask) {
+    int r = ensure_stage(c, n);
+    if (r) return r;
+    CK(cudaMemcpyAsync(c->stage, mask, n, cudaMemcpyHostToDevice, c->stream));
+    dmask = (uint8_t*)c->stage;
+  } else {
+    dmask = (uint8_t*)mask;
+  }
+  uint8_t* nf = nullptr;
+  CK(cudaMalloc(&nf, n));
+  CK(cudaMemsetAsync(c->err_word, 0, sizeof(int), c->stream));
+  if (launch_mask_prepare(c->Q, dmask, nf, (int)c->nx, (int)c->ny, (int)c->nz, c->err_word, c->stream) != 0) {
+    cudaFree(nf);
+    return fail(c, XLB_ERR_ARG, "mask preparation rejected");
+  }
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, c->err_word, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (herr) {
+    cudaFree(nf);
+    return fail(c, XLB_ERR_ARG, "mask holds a code >= 6");
+  }
+  // does the mask hold inlet / outlet cells (adjoint support check)?
+  {
+    std::vector<uint8_t> h;
+    const uint8_t* hp = mask;
+    if (!host_mask) {
+      h.resize(n);
+      CK(cudaMemcpy(h.data(), mask, n, cudaMemcpyDeviceToHost));
+      hp = h.data();
+    }
+    bool io = false;
+    for (size_t k = 0; k < n && !io; ++k) io = (hp[k] == XLB_CELL_INLET || hp[k] == XLB_CELL_OUTLET);
+    c->has_inlet_outlet = io;
+  }
+  if (c->flags) cudaFree(c->flags);
+  c->flags = nf;
+  c->has_mask = true;
+  return XLB_OK;
+}
+
+int xlb_set_bc(xlb_ctx* c, int type, float rho, const float u[3]) {
+  if (!c) return XLB_ERR_ARG;
+  if (!u) return fail(c, XLB_ERR_ARG, "u is null");
+  if (type == XLB_CELL_LID) {
+    c->lid_rho = rho;
+    for (int a = 0; a < 3; ++a) c->lid_u[a] = u[a];
+  } else if (type == XLB_CELL_INLET) {
+    if (!(u[0] < 1.0f)) return fail(c, XLB_ERR_ARG, "inlet u_x must be < 1");
+    for (int a = 0; a < 3; ++a) c->inlet_u[a] = u[a];
+  } else if (type == XLB_CELL_EQ) {
+    if (!(rho > 0.f)) return fail(c, XLB_ERR_ARG, "EQ density must be > 0");
+    c->eq_rho = rho;
+    for (int a = 0; a < 3; ++a) c->eq_u[a] = u[a];
+  } else {
+    return fail(c, XLB_ERR_ARG, "cell type %d carries no boundary value", type);
+  }
+  return XLB_OK;
+}
+
+int xlb_set_force(xlb_ctx* c, const float F[3]) {
+  if (!c) return XLB_ERR_ARG;
+  if (!F) return fail(c, XLB_ERR_ARG, "F is null");
+  for (int a = 0; a < 3; ++a) c->F[a] = (a < c->D) ? F[a] : 0.f;
+  c->has_force = (c->F[0] != 0.f || c->F[1] != 0.f || c->F[2] != 0.f);
+  return XLB_OK;
+}
+
+int xlb_init(xlb_ctx* c, const float* rho, const float* u) {
+  if (!c) return XLB_ERR_ARG;
+  if (c->tape_open) return fail(c, XLB_ERR_STATE, "a tape is open; call xlb_tape_end first");
+  const size_t n = (size_t)c->N;
+  float* dr = c->init_fields;
+  float* du = c->init_fields + n;
+  // copy the caller's fields into the library-owned init fields
+  if (rho) {
+    CK(cudaMemcpyAsync(dr, rho, n * sizeof(float), cudaMemcpyDefault, c->stream));
+  } else {
+    std::vector<float> ones(n, 1.0f);
+    CK(cudaMemcpyAsync(dr, ones.data(), n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  if (u) {
+    CK(cudaMemcpyAsync(du, u, (size_t)c->D * n * sizeof(float), cudaMemcpyDefault, c->stream));
+  } else {
+    CK(cudaMemsetAsync(du, 0, (size_t)c->D * n * sizeof(float), c->stream));
+  }
+  if (!is_device_ptr(rho ? (const void*)rho : (const void*)u)) CK(cudaStreamSynchronize(c->stream));
+  c->has_init = true;
+  int r = launch_init(c, c->buf[c->cur]);
+  if (r) return r;
+  c->kind_h = 0;
+  c->t = 0;
+  return XLB_OK;
+}
+
+static int record_checkpoint(xlb_ctx* c) {
+  if (!c->tape_open || c->tape_k <= 0) return XLB_OK;
+  if (c->t % c->tape_k == 0 && c->t < c->tape_T) {
+    const size_t s = (size_t)(c->t / c->tape_k) - 1;
+    if (s < c->ckpt.size())
+      CK(cudaMemcpyAsync(c->ckpt[s], c->buf[c->cur], state_bytes_raw(c), cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return XLB_OK;
+}
+
+int xlb_step(xlb_ctx* c, int64_t n) {
+  if (!c) return XLB_ERR_ARG;
+  if (n < 0) return fail(c, XLB_ERR_ARG, "n must be >= 0");
+  if (!c->has_init && c->t == 0 && !c->kind_h) return fail(c, XLB_ERR_STATE, "xlb_init (or xlb_state_set) first");
+  if (c->tape_open && c->t + n > c->tape_T)
+    return fail(c, XLB_ERR_STATE, "stepping past the tape length %lld", (long long)c->tape_T);
+  for (int64_t k = 0; k < n; ++k) {
+    int r;
+    if (!c->kind_h) {
+      r = launch_collide_local(c, c->buf[c->cur]);
+      c->kind_h = 1;
+    } else {
+      r = launch_step(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
+      c->cur ^= 1;
+    }
+    if (r) return r;
+    c->t += 1;
+    r = record_checkpoint(c);
+    if (r) return r;
+  }
+  return XLB_OK;
+}
+
+int xlb_get_time(const xlb_ctx* c, int64_t* t) {
+  if (!c || !t) return XLB_ERR_ARG;
+  *t = c->t;
+  return XLB_OK;
+}
+
+int xlb_synchronize(xlb_ctx* c) {
+  if (!c) return XLB_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  return XLB_OK;
+}
+
+int xlb_macroscopic(xlb_ctx* c, float* rho, float* u) {
+  if (!c) return XLB_ERR_ARG;
+  if (!rho && !u) return XLB_OK;
+  const size_t n = (size_t)c->N;
+  const bool host = !is_device_ptr(rho ? (void*)rho : (void*)u);
+  float* dr = rho;
+  float* du = u;
+  if (host) {
+    int r = ensure_stage(c, (1 + c->D) * n * sizeof(float));
+    if (r) return r;
+    dr = rho ? (float*)c->stage : nullptr;
+    du = u ? (float*)c->stage + n : nullptr;
+  }
+  LaunchArgs a = base_args(c);
+  a.src = c->buf[c->cur];
+  a.kind_h = c->kind_h;
+  a.rho_out = dr;
+  a.u_out = du;
+  int r = dispatch(c, OP_MACRO, a);
+  if (r) return r;
+  if (host) {
+    if (rho) CK(cudaMemcpyAsync(rho, dr, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    if (u) CK(cudaMemcpyAsync(u, du, (size_t)c->D * n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return XLB_OK;
+}
+
+int xlb_reduce(xlb_ctx* c, double out_mass[1], double out_mom[3]) {
+  if (!c) return XLB_ERR_ARG;
+  if (!out_mass && !out_mom) return XLB_OK;
+  LaunchArgs a = base_args(c);
+  a.src = c->buf[c->cur];
+  a.kind_h = c->kind_h;
+  int r = dispatch(c, OP_REDUCE_PARTIAL, a);
+  if (r) return r;
+  launch_reduce_final(c->partial, row_blocks(a.p), c->red_out, c->stream);
+  double h[4];
+  CK(cudaMemcpyAsync(h, c->red_out, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (out_mass) out_mass[0] = h[0];
+  if (out_mom)
+    for (int k = 0; k < 3; ++k) out_mom[k] = h[1 + k];
+  return XLB_OK;
+}
+
+// Serialized state: 64-byte header then the raw population buffer.
+struct StateHeader {
+  char magic[8];
+  int32_t Q, storage;
+  int64_t nx, ny, nz, t;
+  int32_t kind_h, reserved;
+};
+static_assert(sizeof(StateHeader) <= 64, "header");
+
+int xlb_state_bytes(const xlb_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return XLB_ERR_ARG;
+  *bytes = 64 + state_bytes_raw(c);
+  return XLB_OK;
+}
+
+int xlb_state_get(xlb_ctx* c, void* buf, size_t bytes) {
+  if (!c || !buf) return XLB_ERR_ARG;
+  if (bytes < 64 + state_bytes_raw(c)) return fail(c, XLB_ERR_ARG, "buffer too small");
+  StateHeader h;
+  memset(&h, 0, sizeof h);
+  memcpy(h.magic, "XLBSTAT1", 8);
+  h.Q = c->Q;
+  h.storage = c->storage;
+  h.nx = c->nx;
+  h.ny = c->ny;
+  h.nz = c->nz;
+  h.t = c->t;
+  h.kind_h = c->kind_h;
+  char hdr[64];
+  memset(hdr, 0, 64);
+  memcpy(hdr, &h, sizeof h);
+  CK(cudaMemcpyAsync(buf, hdr, 64, cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync((char*)buf + 64, c->buf[c->cur], state_bytes_raw(c), cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return XLB_OK;
+}
+
+int xlb_state_set(xlb_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf) return XLB_ERR_ARG;
+  if (c->tape_open) return fail(c, XLB_ERR_STATE, "a tape is open");
+  if (bytes < 64 + state_bytes_raw(c)) return fail(c, XLB_ERR_ARG, "buffer too small");
+  char hdr[64];
+  CK(cudaMemcpy(hdr, buf, 64, cudaMemcpyDefault));
+  StateHeader h;
+  memcpy(&h, hdr, sizeof h);
+  if (memcmp(h.magic, "XLBSTAT1", 8) != 0) return fail(c, XLB_ERR_ARG, "not a serialized xlb state");
+  if (h.Q != c->Q || h.storage != c->storage || h.nx != c->nx || h.ny != c->ny || h.nz != c->nz)
+    return fail(c, XLB_ERR_ARG, "state of a different lattice, size or storage");
+  CK(cudaMemcpyAsync(c->buf[c->cur], (const char*)buf + 64, state_bytes_raw(c), cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->t = h.t;
+  c->kind_h = h.kind_h ? 1 : 0;
+  c->has_init = true;
+  return XLB_OK;
+}
+
+int xlb_populations(xlb_ctx* c, void** ptr, int64_t* plane) {
+  if (!c || !ptr || !plane) return XLB_ERR_ARG;
+  *ptr = c->buf[c->cur];
+  *plane = c->plane;
+  return XLB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// reverse mode
+
+int xlb_tape_end(xlb_ctx* c) {
+  if (!c) return XLB_ERR_ARG;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void* p : c->ckpt) cudaFree(p);
+  for (void* p : c->slots) cudaFree(p);
+  c->ckpt.clear();
+  c->slots.clear();
+  for (int k = 0; k < 2; ++k) {
+    if (c->abar[k]) cudaFree(c->abar[k]);
+    c->abar[k] = nullptr;
+  }
+  c->tape_open = false;
+  c->seg_loaded = -1;
+  c->adj_t = -1;
+  return XLB_OK;
+}
+
+int xlb_tape_begin(xlb_ctx* c, int64_t n_steps, int64_t k) {
+  if (!c) return XLB_ERR_ARG;
+  if (n_steps < 1 || k < 1) return fail(c, XLB_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
+  if (c->t != 0 || c->kind_h || !c->has_init) return fail(c, XLB_ERR_STATE, "open a tape right after xlb_init");
+  if (c->coll == XLB_COLL_KBC) return fail(c, XLB_ERR_UNSUPPORTED, "the adjoint covers BGK and NONE collisions");
+  if (c->has_inlet_outlet) return fail(c, XLB_ERR_UNSUPPORTED, "the adjoint does not cover inlet/outlet cells");
+  xlb_tape_end(c);
+  if (k > n_steps) k = n_steps;
+  const int64_t n_ckpt = (n_steps - 1) / k;
+  const size_t sb = state_bytes_raw(c);
+  for (int64_t s = 0; s < n_ckpt; ++s) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sb);
+    if (e != cudaSuccess) {
+      xlb_tape_end(c);
+      return cuda_fail(c, e, "cudaMalloc(checkpoint)");
+    }
+    c->ckpt.push_back(p);
+  }
+  c->tape_open = true;
+  c->tape_T = n_steps;
+  c->tape_k = k;
+  return XLB_OK;
+}
+
+static int ensure_adjoint_buffers(xlb_ctx* c) {
+  const size_t ab = sizeof(float) * state_elems(c);
+  for (int k = 0; k < 2; ++k)
+    if (!c->abar[k]) CK(cudaMalloc(&c->abar[k], ab));
+  if (c->slots.empty()) {
+    for (int64_t j = 0; j < c->tape_k; ++j) {
+      void* p = nullptr;
+      CK(cudaMalloc(&p, state_bytes_raw(c)));
+      c->slots.push_back(p);
+    }
+  }
+  return XLB_OK;
+}
+
+static AdjointArgs adjoint_args(xlb_ctx* c) {
+  AdjointArgs a;
+  memset(&a, 0, sizeof a);
+  a.p = make_params(c);
+  a.Q = c->Q;
+  a.storage = c->storage;
+  a.coll = c->coll;
+  a.ucs = c->N;
+  a.stream = c->stream;
+  return a;
+}
+
+static int adispatch(xlb_ctx* c, AdjOp op, const AdjointArgs& a) {
+  int r = launch_adjoint(op, a);
+  if (r != 0) return fail(c, XLB_ERR_UNSUPPORTED, "adjoint launch %d rejected (code %d)", (int)op, r);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint kernel launch");
+  return XLB_OK;
+}
+
+int xlb_adjoint_seed_macro(xlb_ctx* c, const float* drho, const float* du) {
+  if (!c) return XLB_ERR_ARG;
+  if (!c->tape_open) return fail(c, XLB_ERR_STATE, "no tape open");
+  if (c->t != c->tape_T || !c->kind_h) return fail(c, XLB_ERR_STATE, "take all %lld taped steps first", (long long)c->tape_T);
+  int r = ensure_adjoint_buffers(c);
+  if (r) return r;
+  const size_t n = (size_t)c->N;
+  const float* dr = drho;
+  const float* duu = du;
+  if ((drho && !is_device_ptr(drho)) || (du && !is_device_ptr(du))) {
+    r = ensure_stage(c, (1 + c->D) * n * sizeof(float));
+    if (r) return r;
+    if (drho) {
+      CK(cudaMemcpyAsync(c->stage, drho, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+      dr = (const float*)c->stage;
+    }
+    if (du) {
+      CK(cudaMemcpyAsync((float*)c->stage + n, du, (size_t)c->D * n * sizeof(float), cudaMemcpyHostToDevice,
+                         c->stream));
+      duu = (const float*)c->stage + n;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  AdjointArgs a = adjoint_args(c);
+  a.state = c->buf[c->cur];
+  a.fields_in = dr;
+  a.fields_in2 = duu;
+  a.abar_out = c->abar[0];
+  r = adispatch(c, ADJ_SEED, a);
+  if (r) return r;
+  c->acur = 0;
+  c->adj_t = c->tape_T;
+  return XLB_OK;
+}
+
+// Recompute the tape slots of segment s (states h_{sk+j-1}, j = 0..k-1; slot
+// 0 of segment 0 is unused since h_{-1} does not exist).
+static int load_segment(xlb_ctx* c, int64_t s) {
+  if (c->seg_loaded == s) return XLB_OK;
+  const int64_t k = c->tape_k;
+  const int64_t jmax = std::min<int64_t>(k - 1, c->tape_T - 1 - s * k);
+  int r;
+  int64_t j0;
+  if (s == 0) {
+    if (jmax < 1) {
+      c->seg_loaded = s;
+      return XLB_OK;
+    }
+    r = launch_init(c, c->slots[1]);
+    if (r) return r;
+    r = launch_collide_local(c, c->slots[1]);
+    if (r) return r;
+    j0 = 2;
+  } else {
+    CK(cudaMemcpyAsync(c->slots[0], c->ckpt[s - 1], state_bytes_raw(c), cudaMemcpyDeviceToDevice, c->stream));
+    j0 = 1;
+  }
+  for (int64_t j = j0; j <= jmax; ++j) {
+    r = launch_step(c, c->slots[j - 1], c->slots[j]);
+    if (r) return r;
+  }
+  c->seg_loaded = s;
+  return XLB_OK;
+}
+
+int xlb_adjoint_step(xlb_ctx* c, int64_t n) {
+  if (!c) return XLB_ERR_ARG;
+  if (!c->tape_open || c->adj_t < 0) return fail(c, XLB_ERR_STATE, "seed the adjoint first");
+  if (n < 0 || n > c->adj_t) return fail(c, XLB_ERR_ARG, "n must lie in [0, %lld]", (long long)c->adj_t);
+  for (int64_t m = 0; m < n; ++m) {
+    const int64_t t = c->adj_t - 1;  // produce fbar_t from fbar_{t+1}
+    AdjointArgs a = adjoint_args(c);
+    a.abar_in = c->abar[c->acur];
+    a.abar_out = c->abar[c->acur ^ 1];
+    int r;
+    if (t >= 1) {
+      const int64_t s = t / c->tape_k;
+      r = load_segment(c, s);
+      if (r) return r;
+      a.state = c->slots[t - s * c->tape_k];
+      cudaEvent_t* pe = prof_begin(c, 1);
+      r = adispatch(c, ADJ_STEP, a);
+      prof_end(c, pe);
+    } else {
+      a.fields_in = c->init_fields;
+      a.fields_in2 = c->init_fields + c->N;
+      r = adispatch(c, ADJ_STEP0, a);
+    }
+    if (r) return r;
+    c->acur ^= 1;
+    c->adj_t = t;
+  }
+  return XLB_OK;
+}
+
+int xlb_adjoint_init_grad(xlb_ctx* c, float* drho0, float* du0) {
+  if (!c) return XLB_ERR_ARG;
+  if (!c->tape_open || c->adj_t != 0) return fail(c, XLB_ERR_STATE, "run the adjoint back to step 0 first");
+  if (!drho0 && !du0) return XLB_OK;
+  const size_t n = (size_t)c->N;
+  const bool host = !is_device_ptr(drho0 ? (void*)drho0 : (void*)du0);
+  float* dr = drho0;
+  float* du = du0;
+  if (host) {
+    int r = ensure_stage(c, (1 + c->D) * n * sizeof(float));
+    if (r) return r;
+    dr = drho0 ? (float*)c->stage : nullptr;
+    du = du0 ? (float*)c->stage + n : nullptr;
+  }
+  AdjointArgs a = adjoint_args(c);
+  a.abar_in = c->abar[c->acur];
+  a.fields_in = c->init_fields;
+  a.fields_in2 = c->init_fields + c->N;
+  a.grad_rho = dr;
+  a.grad_u = du;
+  int r = adispatch(c, ADJ_INIT_GRAD, a);
+  if (r) return r;
+  if (host) {
+    if (drho0) CK(cudaMemcpyAsync(drho0, dr, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    if (du0) CK(cudaMemcpyAsync(du0, du, (size_t)c->D * n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return XLB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// profiling
+
+int xlb_profile_enable(xlb_ctx* c, int on) {
+  if (!c) return XLB_ERR_ARG;
+  c->prof = on != 0;
+  c->ev_used = 0;
+  return XLB_OK;
+}
+
+int xlb_profile_read(xlb_ctx* c, int kernel, double* total_ms, int64_t* launches) {
+  if (!c || !total_ms || !launches) return XLB_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  double tot = 0.0;
+  int64_t cnt = 0;
+  for (size_t k = 0; k < c->ev_used; ++k) {
+    if (c->ev_kind[k] != kernel) continue;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev_pool[k].a, c->ev_pool[k].b));
+    tot += ms;
+    ++cnt;
+  }
+  *total_ms = tot;
+  *launches = cnt;
+  c->ev_used = 0;
+  return XLB_OK;
+}
+
+}  // extern "C"

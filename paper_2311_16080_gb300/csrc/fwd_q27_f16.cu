@@ -1,0 +1,6 @@
+// Forward kernels instantiated for Q = 27, f16 storage.
+#include "kernels.cuh"
+
+namespace xlb {
+int launch_fwd_q27_s1(Op op, const LaunchArgs& a) { return launch_typed<27, __half>(op, a); }
+}  // namespace xlb

@@ -1,0 +1,237 @@
+// Device functions of the fused stream-collide update: neighbour addressing,
+// the pull stream with the mask's boundary rules, moments, equilibrium, BGK
+// and KBC collisions and the exact-difference body force.
+//
+// All arithmetic is FP32 on deviations df_i = f_i - w_i (rho0 = 1):
+//   rho = 1 + sum_i df_i                       (Eq. 6)
+//   j   = sum_i c_i df_i, u = j / rho          (Eq. 7; sum_i c_i w_i = 0)
+//   df_i^eq = w_i [drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)]   (Eq. 5)
+#pragma once
+#include "lattice.cuh"
+#include "xlb_types.h"
+
+namespace xlb {
+
+enum Collision { COLL_NONE = 0, COLL_BGK = 1, COLL_KBC = 2 };
+
+// Periodic neighbour coordinates of one cell: xo[k] = x + k - 1 wrapped, and
+// rb[b][c] = row offset of (y + b - 1, z + c - 1) wrapped.  The source of
+// direction i is xo[1 - cx] + rb[1 - cy][1 - cz].
+struct Nbr {
+  int xo[3];
+  long long rb[3][3];
+};
+
+__device__ __forceinline__ int wrap_m(int v, int n) { return v == 0 ? n - 1 : v - 1; }
+__device__ __forceinline__ int wrap_p(int v, int n) { return v == n - 1 ? 0 : v + 1; }
+
+__device__ __forceinline__ void make_nbr(Nbr& nb, int x, int y, int z, int nx, int ny, int nz) {
+  nb.xo[0] = wrap_m(x, nx);
+  nb.xo[1] = x;
+  nb.xo[2] = wrap_p(x, nx);
+  const int ys[3] = {wrap_m(y, ny), y, wrap_p(y, ny)};
+  const int zs[3] = {nz > 1 ? wrap_m(z, nz) : 0, z, nz > 1 ? wrap_p(z, nz) : 0};
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nb.rb[b][c] = (long long)nx * ((long long)ys[b] + (long long)ny * zs[c]);
+}
+
+template <int Q>
+__device__ __forceinline__ long long src_index(const Nbr& nb, int i) {
+  return nb.xo[1 - Lattice<Q>::c(i, 0)] + nb.rb[1 - Lattice<Q>::c(i, 1)][1 - Lattice<Q>::c(i, 2)];
+}
+
+// Pull without boundary rules: df_i(x) = h_i(x - c_i), periodic (Eq. 2).
+template <int Q, typename S>
+__device__ __forceinline__ void pull_periodic(const S* __restrict__ src, long long plane, const Nbr& nb,
+                                              float (&df)[Q]) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) df[i] = Store<S>::ld(src + (long long)i * plane + src_index<Q>(nb, i));
+}
+
+// Pull with the mask rules for a source cell x - c_i of type
+//   fluid-like: h_i(x - c_i);   WALL: h_opp(i)(x);
+//   LID: h_opp(i)(x) + 2 w_i rho_w (c_i . u_w) / cs^2;   EQ: f_i^eq(rho_w, u_w).
+template <int Q, typename S>
+__device__ __forceinline__ void pull_masked(const S* __restrict__ src, const StepParams& p, const Nbr& nb,
+                                            long long self, float (&df)[Q]) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const long long s = src_index<Q>(nb, i);
+    const int t = p.flags[s] & FLAG_TYPE;
+    if (fluid_like(t)) {
+      df[i] = Store<S>::ld(src + (long long)i * p.plane + s);
+    } else if (t == EQ) {
+      df[i] = p.eq_df[i];
+    } else {
+      float v = Store<S>::ld(src + (long long)opposite<Q>(i) * p.plane + self);
+      if (t == LID) v += p.lid_term[i];
+      df[i] = v;
+    }
+  }
+}
+
+// Zou-He velocity inlet (inflow along +x; unknown populations have c_x = +1):
+//   rho = [sum_{c_x=0} f_i + 2 sum_{c_x=-1} f_i] / (1 - u_x),
+//   f_i = f_opp(i) + f_i^eq - f_opp(i)^eq = f_opp(i) + 6 w_i rho (c_i . u).
+// In deviations the rest parts of the numerator sum to exactly 1.
+template <int Q>
+__device__ __forceinline__ void zou_he_inlet(const StepParams& p, float (&df)[Q]) {
+  float s = 1.0f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (Lattice<Q>::c(i, 0) == 0) s += df[i];
+    if (Lattice<Q>::c(i, 0) == -1) s += 2.0f * df[i];
+  }
+  const float rho = s / (1.0f - p.inlet_u[0]);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (Lattice<Q>::c(i, 0) == 1) {
+      float cu = Lattice<Q>::c(i, 0) * p.inlet_u[0] + Lattice<Q>::c(i, 1) * p.inlet_u[1];
+      if (Lattice<Q>::D == 3) cu += Lattice<Q>::c(i, 2) * p.inlet_u[2];
+      df[i] = df[opposite<Q>(i)] + 6.0f * weight<Q>(i) * rho * cu;
+    }
+  }
+}
+
+// Full post-stream populations of a fluid-like cell with every boundary rule:
+// mask substitution, then Zou-He on INLET cells, then the zero-gradient
+// outflow on OUTLET cells (c_x = -1 populations taken from the cell at x - 1).
+template <int Q, typename S>
+__device__ __forceinline__ void pull_cell(const S* __restrict__ src, const StepParams& p, int x, int y, int z,
+                                          long long self, int type, const Nbr& nb, float (&df)[Q]) {
+  pull_masked<Q, S>(src, p, nb, self, df);
+  if (type == INLET) zou_he_inlet<Q>(p, df);
+  if (type == OUTLET) {
+    const int xl = wrap_m(x, p.nx);
+    Nbr nl;
+    make_nbr(nl, xl, y, z, p.nx, p.ny, p.nz);
+    float dl[Q];
+    pull_masked<Q, S>(src, p, nl, self - x + xl, dl);
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      if (Lattice<Q>::c(i, 0) == -1) df[i] = dl[i];
+  }
+}
+
+template <int Q>
+__device__ __forceinline__ void moments(const float (&df)[Q], float& drho, float (&j)[3]) {
+  drho = 0.f;
+  j[0] = j[1] = j[2] = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    drho += df[i];
+    if (Lattice<Q>::c(i, 0)) j[0] += Lattice<Q>::c(i, 0) * df[i];
+    if (Lattice<Q>::c(i, 1)) j[1] += Lattice<Q>::c(i, 1) * df[i];
+    if (Lattice<Q>::c(i, 2)) j[2] += Lattice<Q>::c(i, 2) * df[i];
+  }
+}
+
+// Bracket of Eq. 5 without the leading 1: 3 c.u + 4.5 (c.u)^2 - 1.5 u.u
+template <int Q>
+__device__ __forceinline__ float eq_poly(int i, const float (&u)[3], float usq) {
+  float cu = 0.f;
+  if (Lattice<Q>::c(i, 0)) cu += Lattice<Q>::c(i, 0) * u[0];
+  if (Lattice<Q>::c(i, 1)) cu += Lattice<Q>::c(i, 1) * u[1];
+  if (Lattice<Q>::c(i, 2)) cu += Lattice<Q>::c(i, 2) * u[2];
+  return cu * (3.0f + 4.5f * cu) - 1.5f * usq;
+}
+
+// Exact-difference body force: df_i += f_i^eq(rho, u + F/rho) - f_i^eq(rho, u).
+template <int Q>
+__device__ __forceinline__ void add_force(float (&df)[Q], float rho, const float (&u)[3], float usq,
+                                          const float (&F)[3]) {
+  const float ir = 1.0f / rho;
+  float v[3] = {u[0] + F[0] * ir, u[1] + F[1] * ir, u[2] + F[2] * ir};
+  if (Lattice<Q>::D == 2) v[2] = 0.f;
+  const float vsq = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) df[i] += weight<Q>(i) * rho * (eq_poly<Q>(i, v, vsq) - eq_poly<Q>(i, u, usq));
+}
+
+// Collision C of Eq. 1 on one fluid-like cell, in place on deviations.
+//   BGK (Eq. 3): df_i += omega (df_i^eq - df_i)
+//   KBC (Karlin, Bosch, Chikatamarla 2014): f^neq = ds + dh, beta = omega / 2,
+//     gamma = 1/beta - (2 - 1/beta) <ds|dh> / <dh|dh>,  <a|b> = sum a_i b_i / f_i^eq,
+//     f_i <- f_i - beta (2 ds_i + gamma dh_i)
+//   where ds carries the deviatoric second moments of f^neq on the natural
+//   moment basis: ds_i = D_aa / 2 for c_i = +-e_a, ds_i = c_ia c_ib Pi_ab / 4
+//   for c_i with two non-zero components a, b, and 0 otherwise
+//   (D_aa = Pi_aa - tr(Pi) / d).
+template <int Q, int COLL>
+__device__ __forceinline__ void collide(float (&df)[Q], const StepParams& p) {
+  if (COLL == COLL_NONE) return;
+  float drho, j[3];
+  moments<Q>(df, drho, j);
+  const float rho = 1.0f + drho;
+  const float ir = 1.0f / rho;
+  float u[3] = {j[0] * ir, j[1] * ir, j[2] * ir};
+  if (Lattice<Q>::D == 2) u[2] = 0.f;
+  const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  float force_u[3];
+  if (p.has_force) {
+    force_u[0] = u[0];
+    force_u[1] = u[1];
+    force_u[2] = u[2];
+  }
+  if (COLL == COLL_BGK) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const float dfeq = weight<Q>(i) * (drho + rho * eq_poly<Q>(i, u, usq));
+      df[i] = fmaf(p.omega, dfeq - df[i], df[i]);
+    }
+  } else {
+    // KBC: non-equilibrium part and its second moments
+    float fneq[Q], feq[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const float poly = eq_poly<Q>(i, u, usq);
+      const float dfeq = weight<Q>(i) * (drho + rho * poly);
+      fneq[i] = df[i] - dfeq;
+      feq[i] = weight<Q>(i) * rho * (1.0f + poly);
+    }
+    float P[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b)
+          if (Lattice<Q>::c(i, a) * Lattice<Q>::c(i, b) != 0)
+            P[a][b] += (float)(Lattice<Q>::c(i, a) * Lattice<Q>::c(i, b)) * fneq[i];
+    }
+    constexpr float inv_d = 1.0f / Lattice<Q>::D;
+    const float tr = P[0][0] + P[1][1] + P[2][2];
+    float sh = 0.f, hh = 0.f;
+    float ds[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      float s = 0.f;
+      if (nnz<Q>(i) == 1) {
+        const int a = Lattice<Q>::c(i, 0) ? 0 : (Lattice<Q>::c(i, 1) ? 1 : 2);
+        s = 0.5f * (P[a][a] - tr * inv_d);
+      } else if (nnz<Q>(i) == 2) {
+        const int a = Lattice<Q>::c(i, 0) ? 0 : 1;
+        const int b = Lattice<Q>::c(i, 2) ? 2 : 1;
+        s = 0.25f * (float)(Lattice<Q>::c(i, a) * Lattice<Q>::c(i, b)) * P[a][b];
+      }
+      ds[i] = s;
+      const float dh = fneq[i] - s;
+      const float ife = 1.0f / feq[i];
+      sh = fmaf(s * dh, ife, sh);
+      hh = fmaf(dh * dh, ife, hh);
+    }
+    const float beta = 0.5f * p.omega;
+    const float ib = 1.0f / beta;
+    const float gamma = (hh < 1e-20f) ? 2.0f : ib - (2.0f - ib) * sh / hh;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const float dh = fneq[i] - ds[i];
+      df[i] -= beta * (2.0f * ds[i] + gamma * dh);
+    }
+  }
+  if (p.has_force) add_force<Q>(df, rho, force_u, usq, p.F);
+}
+
+}  // namespace xlb

@@ -1,0 +1,44 @@
+// Plain-old-data structures shared by the host side of the library and its
+// kernels.  No CUDA or torch types: this header compiles as C++ on the host.
+#pragma once
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define XLB_HD __host__ __device__
+#else
+#define XLB_HD
+#endif
+
+namespace xlb {
+
+// Cell types of the mask (Section 3.5); values are the public ABI codes.
+enum CellType : uint8_t { FLUID = 0, WALL = 1, LID = 2, INLET = 3, OUTLET = 4, EQ = 5 };
+
+// Derived per-cell flag byte written by the mask preparation kernel:
+// bits 0-2 hold the cell type, bit 3 marks a fluid-like cell whose update
+// needs the per-direction boundary rules (a non-fluid cell in its stencil, or
+// an inlet / outlet cell itself).
+constexpr uint8_t FLAG_TYPE = 0x07;
+constexpr uint8_t FLAG_SLOW = 0x08;
+
+XLB_HD inline bool fluid_like(int t) { return t == FLUID || t == INLET || t == OUTLET; }
+
+// Everything one stream-collide launch needs besides the two buffers.
+struct StepParams {
+  int nx, ny, nz;        // lattice extents (nz = 1 for D2Q9)
+  long long plane;       // elements between consecutive population planes
+  float omega;           // dt / tau (Eq. 3, Eq. 4)
+  int has_mask;          // 0: every cell is fluid and every face periodic
+  const uint8_t* flags;  // derived flag byte per cell (FLAG_*), or null
+  int has_force;         // exact-difference body force on fluid-like cells
+  float F[3];
+  float lid_term[27];    // 2 w_i rho_w (c_i . u_lid) / cs^2 for a LID source
+  float eq_df[27];       // f_i^eq(rho_eq, u_eq) - w_i (equilibrium-BC cells)
+  float eq_rho, eq_u[3];
+  float inlet_u[3];      // Zou-He inlet velocity
+};
+
+// Deviation storage: populations are stored as f_i - w_i * RHO0.
+constexpr float RHO0 = 1.0f;
+
+}  // namespace xlb

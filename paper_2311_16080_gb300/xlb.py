@@ -1,0 +1,326 @@
+"""Thin Python binding of libxlb.so (include/xlb.h): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps and raises
+``XlbError`` on a non-zero status.  Buffers may be torch tensors (host or
+CUDA; their ``data_ptr()`` is passed), numpy arrays or raw integer addresses.
+Every step of the lattice Boltzmann path runs in the library's CUDA kernels;
+if the library is missing, loading raises instead of falling back to any
+CPU implementation.
+
+``Simulation`` is a small convenience wrapper over one ctx, and
+``KineticEnergyRollout`` / ``rollout`` expose the adjoint to torch autograd.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libxlb.so")
+
+XLB_OK, XLB_ERR_ARG, XLB_ERR_UNSUPPORTED, XLB_ERR_OOM, XLB_ERR_CUDA, XLB_ERR_TIMEOUT, XLB_ERR_STATE = range(7)
+XLB_D2Q9, XLB_D3Q19, XLB_D3Q27 = 9, 19, 27
+XLB_COLL_NONE, XLB_COLL_BGK, XLB_COLL_KBC = 0, 1, 2
+XLB_STORE_F32, XLB_STORE_F16, XLB_STORE_BF16 = 0, 1, 2
+XLB_CELL_FLUID, XLB_CELL_WALL, XLB_CELL_LID, XLB_CELL_INLET, XLB_CELL_OUTLET, XLB_CELL_EQ = range(6)
+
+STORAGE = {"f32": XLB_STORE_F32, "f16": XLB_STORE_F16, "bf16": XLB_STORE_BF16}
+COLLISION = {"none": XLB_COLL_NONE, "bgk": XLB_COLL_BGK, "kbc": XLB_COLL_KBC}
+
+
+class XlbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+_vp, _i, _i64, _d, _f = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_float
+_PROTOS = {
+    "xlb_create": (_i, [C.POINTER(_vp), _i, C.POINTER(_i64), _d, _i, _i, _vp]),
+    "xlb_destroy": (None, [_vp]),
+    "xlb_last_error": (C.c_char_p, [_vp]),
+    "xlb_status_string": (C.c_char_p, [_i]),
+    "xlb_omega_from_nu": (_d, [_d]),
+    "xlb_set_mask": (_i, [_vp, _vp]),
+    "xlb_set_bc": (_i, [_vp, _i, _f, C.POINTER(_f)]),
+    "xlb_set_force": (_i, [_vp, C.POINTER(_f)]),
+    "xlb_init": (_i, [_vp, _vp, _vp]),
+    "xlb_step": (_i, [_vp, _i64]),
+    "xlb_get_time": (_i, [_vp, C.POINTER(_i64)]),
+    "xlb_macroscopic": (_i, [_vp, _vp, _vp]),
+    "xlb_reduce": (_i, [_vp, C.POINTER(_d), C.POINTER(_d)]),
+    "xlb_synchronize": (_i, [_vp]),
+    "xlb_state_bytes": (_i, [_vp, C.POINTER(C.c_size_t)]),
+    "xlb_state_get": (_i, [_vp, _vp, C.c_size_t]),
+    "xlb_state_set": (_i, [_vp, _vp, C.c_size_t]),
+    "xlb_populations": (_i, [_vp, C.POINTER(_vp), C.POINTER(_i64)]),
+    "xlb_tape_begin": (_i, [_vp, _i64, _i64]),
+    "xlb_adjoint_seed_macro": (_i, [_vp, _vp, _vp]),
+    "xlb_adjoint_step": (_i, [_vp, _i64]),
+    "xlb_adjoint_init_grad": (_i, [_vp, _vp, _vp]),
+    "xlb_tape_end": (_i, [_vp]),
+    "xlb_profile_enable": (_i, [_vp, _i]),
+    "xlb_profile_read": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_i64)]),
+}
+
+
+def load(path=None):
+    """Load libxlb.so (built in-tree by ``paper_2311_16080_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libxlb.so not found at {path}; build it with "
+                           "`python -m paper_2311_16080_gb300.build` (there is no CPU fallback)")
+    lib = C.CDLL(path)
+    for name, (res, args) in _PROTOS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _status_name(s):
+    try:
+        return load().xlb_status_string(s).decode()
+    except Exception:
+        return f"status {s}"
+
+
+def _ptr(buf):
+    """Address of a buffer: torch tensor, numpy array, int or None."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("buffers must be contiguous")
+        return buf.data_ptr()
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return buf.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _check(status, ctx=None):
+    if status != XLB_OK:
+        msg = load().xlb_last_error(ctx).decode(errors="replace")
+        raise XlbError(status, msg)
+
+
+def _vec3(v):
+    v = list(v) + [0.0] * (3 - len(v))
+    return (C.c_float * 3)(*[float(x) for x in v[:3]])
+
+
+# ---- one wrapper per C entry point ------------------------------------------
+
+def xlb_create(lattice, dims, omega, collision=XLB_COLL_BGK, storage=XLB_STORE_F32, cuda_stream=None):
+    lib = load()
+    out = C.c_void_p()
+    d = list(dims) + [1] * (3 - len(dims))
+    arr = (C.c_int64 * 3)(*[int(x) for x in d])
+    _check(lib.xlb_create(C.byref(out), int(lattice), arr, float(omega), int(collision), int(storage),
+                          cuda_stream))
+    return out.value
+
+
+def xlb_destroy(ctx):
+    load().xlb_destroy(ctx)
+
+
+def xlb_last_error(ctx=None):
+    return load().xlb_last_error(ctx).decode()
+
+
+def xlb_status_string(status):
+    return load().xlb_status_string(int(status)).decode()
+
+
+def xlb_omega_from_nu(nu):
+    return load().xlb_omega_from_nu(float(nu))
+
+
+def xlb_set_mask(ctx, mask):
+    _check(load().xlb_set_mask(ctx, _ptr(mask)), ctx)
+
+
+def xlb_set_bc(ctx, cell_type, rho, u):
+    _check(load().xlb_set_bc(ctx, int(cell_type), float(rho), _vec3(u)), ctx)
+
+
+def xlb_set_force(ctx, F):
+    _check(load().xlb_set_force(ctx, _vec3(F)), ctx)
+
+
+def xlb_init(ctx, rho=None, u=None):
+    _check(load().xlb_init(ctx, _ptr(rho), _ptr(u)), ctx)
+
+
+def xlb_step(ctx, n):
+    _check(load().xlb_step(ctx, int(n)), ctx)
+
+
+def xlb_get_time(ctx):
+    t = C.c_int64()
+    _check(load().xlb_get_time(ctx, C.byref(t)), ctx)
+    return t.value
+
+
+def xlb_macroscopic(ctx, rho=None, u=None):
+    _check(load().xlb_macroscopic(ctx, _ptr(rho), _ptr(u)), ctx)
+
+
+def xlb_reduce(ctx):
+    m = (C.c_double * 1)()
+    j = (C.c_double * 3)()
+    _check(load().xlb_reduce(ctx, m, j), ctx)
+    return m[0], [j[0], j[1], j[2]]
+
+
+def xlb_synchronize(ctx):
+    _check(load().xlb_synchronize(ctx), ctx)
+
+
+def xlb_state_bytes(ctx):
+    n = C.c_size_t()
+    _check(load().xlb_state_bytes(ctx, C.byref(n)), ctx)
+    return n.value
+
+
+def xlb_state_get(ctx, buf=None):
+    if buf is None:
+        buf = np.empty(xlb_state_bytes(ctx), dtype=np.uint8)
+    nbytes = buf.nbytes if hasattr(buf, "nbytes") else buf.numel() * buf.element_size()
+    _check(load().xlb_state_get(ctx, _ptr(buf), nbytes), ctx)
+    return buf
+
+
+def xlb_state_set(ctx, buf):
+    nbytes = buf.nbytes if hasattr(buf, "nbytes") else buf.numel() * buf.element_size()
+    _check(load().xlb_state_set(ctx, _ptr(buf), nbytes), ctx)
+
+
+def xlb_populations(ctx):
+    p = C.c_void_p()
+    s = C.c_int64()
+    _check(load().xlb_populations(ctx, C.byref(p), C.byref(s)), ctx)
+    return p.value, s.value
+
+
+def xlb_tape_begin(ctx, n_steps, checkpoint_every):
+    _check(load().xlb_tape_begin(ctx, int(n_steps), int(checkpoint_every)), ctx)
+
+
+def xlb_adjoint_seed_macro(ctx, dL_drho=None, dL_du=None):
+    _check(load().xlb_adjoint_seed_macro(ctx, _ptr(dL_drho), _ptr(dL_du)), ctx)
+
+
+def xlb_adjoint_step(ctx, n):
+    _check(load().xlb_adjoint_step(ctx, int(n)), ctx)
+
+
+def xlb_adjoint_init_grad(ctx, dL_drho0=None, dL_du0=None):
+    _check(load().xlb_adjoint_init_grad(ctx, _ptr(dL_drho0), _ptr(dL_du0)), ctx)
+
+
+def xlb_tape_end(ctx):
+    _check(load().xlb_tape_end(ctx), ctx)
+
+
+def xlb_profile_enable(ctx, on=True):
+    _check(load().xlb_profile_enable(ctx, int(bool(on))), ctx)
+
+
+def xlb_profile_read(ctx, kernel=0):
+    ms = C.c_double()
+    n = C.c_int64()
+    _check(load().xlb_profile_read(ctx, int(kernel), C.byref(ms), C.byref(n)), ctx)
+    return ms.value, n.value
+
+
+# ---- convenience wrapper -------------------------------------------------------
+
+class Simulation:
+    """One simulation context.  Fields use the library layout: scalars
+    ``[nz, ny, nx]`` (or ``[ny, nx]``), vectors ``[D, ...]``."""
+
+    def __init__(self, lattice, dims, omega, collision="bgk", storage="f32", stream=None):
+        self.Q = int(lattice)
+        self.D = 2 if self.Q == 9 else 3
+        self.dims = tuple(int(x) for x in dims) + (1,) * (3 - len(dims))
+        self.shape = (self.dims[1], self.dims[0]) if self.D == 2 else (self.dims[2], self.dims[1], self.dims[0])
+        self.N = int(np.prod(self.shape))
+        self.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
+        self.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        self.ctx = xlb_create(self.Q, self.dims, omega, self.collision, self.storage, stream)
+
+    def close(self):
+        if self.ctx:
+            xlb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_mask(self, mask):
+        xlb_set_mask(self.ctx, mask)
+
+    def set_bc(self, cell_type, rho=1.0, u=(0.0, 0.0, 0.0)):
+        xlb_set_bc(self.ctx, cell_type, rho, u)
+
+    def set_force(self, F):
+        xlb_set_force(self.ctx, F)
+
+    def init(self, rho=None, u=None):
+        xlb_init(self.ctx, rho, u)
+
+    def step(self, n=1):
+        xlb_step(self.ctx, n)
+
+    @property
+    def time(self):
+        return xlb_get_time(self.ctx)
+
+    def macroscopic(self, rho=None, u=None):
+        """Fill (or allocate as numpy float32) rho [shape] and u [D, shape]."""
+        if rho is None:
+            rho = np.empty(self.shape, np.float32)
+        if u is None:
+            u = np.empty((self.D,) + self.shape, np.float32)
+        xlb_macroscopic(self.ctx, rho, u)
+        return rho, u
+
+    def reduce(self):
+        return xlb_reduce(self.ctx)
+
+    def synchronize(self):
+        xlb_synchronize(self.ctx)
+
+    def state_get(self):
+        return xlb_state_get(self.ctx)
+
+    def state_set(self, buf):
+        xlb_state_set(self.ctx, buf)
+
+    def populations(self):
+        """(raw host copy of the stored deviations as [Q, shape] in the storage
+        dtype, kind_h) from a state snapshot."""
+        buf = self.state_get()
+        kind_h = int(np.frombuffer(buf[:64].tobytes(), dtype=np.int32)[12])
+        dt = {0: np.float32, 1: np.float16, 2: np.uint16}[self.storage]
+        raw = np.frombuffer(buf[64:].tobytes(), dtype=dt)
+        align = 256 // raw.itemsize
+        plane = (self.N + align - 1) // align * align
+        return raw.reshape(self.Q, plane)[:, :self.N].reshape((self.Q,) + self.shape), kind_h

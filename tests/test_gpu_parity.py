@@ -1,0 +1,211 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (relative L2 over the compared cells):
+  stream only (collision NONE): bit-exact, every storage type;
+  FP32 storage, FP32 arithmetic: u <= 1e-4 after 1000 steps (Taylor-Green),
+    and the same bound on the shorter boundary / KBC / force cases;
+  FP16 storage of shifted populations: u <= 5e-3; BF16: reported, <= 5e-2
+    (its 8-bit mantissa puts it above the FP16 bound by design).
+"""
+import numpy as np
+import pytest
+
+from oracle import lbm as O
+from paper_2311_16080_gb300 import inputs as I
+from paper_2311_16080_gb300 import xlb as X
+from parity_util import Case, f64_to_raw, raw_to_f64, rel_l2, storage_dtype
+
+pytestmark = pytest.mark.gpu
+
+
+def _set_raw_state(sim, raw, kind_h):
+    """Write raw stored deviations [Q, shape] into the simulation."""
+    buf = sim.state_get().copy()
+    hdr = buf[:64].view(np.int32)
+    hdr[12] = kind_h
+    data = buf[64:].view(raw.dtype)
+    align = 256 // raw.itemsize
+    plane = (sim.N + align - 1) // align * align
+    data = data.reshape(sim.Q, plane)
+    data[:, :sim.N] = raw.reshape(sim.Q, sim.N)
+    sim.state_set(buf)
+
+
+@pytest.mark.parametrize("q,shape", [(9, (37, 45)), (19, (6, 9, 70)), (27, (5, 7, 33))])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_stream_only_is_bit_exact(q, shape, storage):
+    """Collision NONE: n steps are a pure permutation, bit for bit."""
+    lat = O.Lattice(q)
+    dims = tuple(reversed(shape))
+    sim = X.Simulation(q, dims, 1.0, "none", storage)
+    sim.init()
+    rng = np.random.default_rng(q)
+    vals = rng.uniform(-0.05, 0.05, (q,) + shape)
+    if storage == "bf16":
+        raw = (vals.astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+    else:
+        raw = vals.astype(storage_dtype(storage))
+    _set_raw_state(sim, raw, kind_h=1)
+    n = 5
+    sim.step(n)
+    got, kind = sim.populations()
+    assert kind == 1
+    h = raw_to_f64(raw, storage)
+    mask = np.zeros(shape, np.uint8)
+    bc = O.BC(lat.d)
+    for _ in range(n):
+        h = O.stream_bc(lat, h, mask, bc)
+    assert np.array_equal(got.view(np.uint8), f64_to_raw(h, storage).view(np.uint8))
+    sim.close()
+
+
+def _tg_case(n=128, omega=1.25, collision="bgk"):
+    rho, u = I.taylor_green_2d(n, n, u0=0.04)
+    return Case(9, (n, n), omega, collision, rho0=rho, u0=u)
+
+
+def test_taylor_green_fp32_1000_steps():
+    c = _tg_case()
+    (rho_o, u_o), _ = c.oracle(1000)
+    rho_g, u_g = c.gpu(1000, "f32")
+    assert rel_l2(u_g, u_o) <= 1e-4
+    assert rel_l2(rho_g - 1, rho_o - 1) <= 1e-3
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 5e-3), ("bf16", 5e-2)])
+def test_taylor_green_low_precision_storage(storage, tol):
+    c = _tg_case()
+    (rho_o, u_o), _ = c.oracle(1000)
+    rho_g, u_g = c.gpu(1000, storage)
+    err = rel_l2(u_g, u_o)
+    print(f"{storage} storage: rel-L2(u) after 1000 steps = {err:.3e}")
+    assert err <= tol
+
+
+def test_taylor_green_kbc_fp32():
+    c = _tg_case(64, omega=1.9, collision="kbc")
+    (_, u_o), _ = c.oracle(300)
+    _, u_g = c.gpu(300)
+    assert rel_l2(u_g, u_o) <= 1e-4
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_periodic_random_flow(q):
+    shape = (10, 12, 40)
+    rho, u = I.random_flow(shape, 3, seed=3, rho_amp=0.01, u_amp=0.03)
+    c = Case(q, shape, 1.7, "bgk", rho0=rho, u0=u)
+    (rho_o, u_o), _ = c.oracle(60)
+    rho_g, u_g = c.gpu(60)
+    assert rel_l2(u_g, u_o) <= 1e-4
+    assert rel_l2(rho_g - 1, rho_o - 1) <= 1e-4
+
+
+def test_lid_driven_cavity_d3q19():
+    n = 20
+    mask = I.lid_driven_cavity_mask(n)
+    c = Case(19, mask.shape, 1.6, "bgk", mask=mask, lid=(1.0, (0.05, 0.0, 0.0)))
+    (rho_o, u_o), _ = c.oracle(300)
+    rho_g, u_g = c.gpu(300)
+    fl = mask == 0
+    assert rel_l2(u_g[:, fl], u_o[:, fl]) <= 1e-4
+    assert np.all(rho_g[~fl] == 0) and np.all(u_g[:, ~fl] == 0)
+
+
+def test_mixed_boundaries_and_force_d2q9():
+    shape = (40, 48)
+    mask = I.channel_2d_mask(48, 40, top=O.LID)
+    mask[I.random_obstacle_mask(shape, 0.08, seed=5) > 0] = O.WALL
+    mask[I.random_obstacle_mask(shape, 0.03, seed=6) > 0] = O.EQ
+    rho, u = I.random_flow(shape, 2, seed=7, rho_amp=0.005, u_amp=0.02)
+    c = Case(9, shape, 1.3, "bgk", mask=mask, force=(2e-5, -1e-5, 0.0), lid=(1.0, (0.04, 0.0, 0.0)),
+             eq=(1.01, (0.01, -0.02, 0.0)), rho0=rho, u0=u)
+    (rho_o, u_o), _ = c.oracle(200)
+    rho_g, u_g = c.gpu(200)
+    fl = O.fluid_like(mask)
+    assert rel_l2(u_g[:, fl], u_o[:, fl]) <= 1e-4
+    assert rel_l2(rho_g[fl] - 1, rho_o[fl] - 1) <= 1e-3
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-4), ("f16", 5e-3), ("bf16", 5e-2)])
+def test_kbc_sphere_channel_d3q27(storage, tol):
+    """Zou-He inlet, outflow, halfway bounce-back sphere, KBC, D3Q27."""
+    mask = I.sphere_channel_mask(48, 16, 16, radius=4, center=(14, 8, 8))
+    uin = (0.04, 0.0, 0.0)
+    rho = np.ones(mask.shape)
+    u = np.zeros((3,) + mask.shape)
+    u[0][O.fluid_like(mask)] = uin[0]
+    c = Case(27, mask.shape, 1.6, "kbc", mask=mask, inlet=uin, rho0=rho, u0=u)
+    (rho_o, u_o), _ = c.oracle(150)
+    rho_g, u_g = c.gpu(150, storage)
+    fl = O.fluid_like(mask)
+    err = rel_l2(u_g[:, fl], u_o[:, fl])
+    print(f"KBC D3Q27 {storage}: rel-L2(u) = {err:.3e}")
+    assert err <= tol
+
+
+def test_reduce_matches_macroscopic_and_conserves_mass():
+    mask = I.lid_driven_cavity_mask(24)
+    mask[mask == O.LID] = O.WALL
+    rho, u = I.random_flow(mask.shape, 3, seed=9, rho_amp=0.01, u_amp=0.02)
+    c = Case(19, mask.shape, 1.5, "bgk", mask=mask, rho0=rho, u0=u)
+    sim = c.gpu_sim()
+    m0, _ = sim.reduce()
+    r, _ = sim.macroscopic()
+    assert abs(m0 - r.astype(np.float64).sum()) < 1e-9 * m0
+    sim.step(500)
+    m1, _ = sim.reduce()
+    assert abs(m1 - m0) < 2e-6 * m0
+    sim.close()
+
+
+def test_state_roundtrip_resumes_identically():
+    c = _tg_case(64)
+    a = c.gpu_sim()
+    a.step(37)
+    snap = a.state_get()
+    a.step(20)
+    ra, ua = a.macroscopic()
+    b = c.gpu_sim()
+    b.state_set(snap)
+    assert b.time == 37
+    b.step(20)
+    rb, ub = b.macroscopic()
+    assert np.array_equal(ra, rb) and np.array_equal(ua, ub)
+    a.close()
+    b.close()
+
+
+def test_full_size_cavity_sampled_step():
+    """256^3 lid-driven cavity in the benchmark's configuration: after some
+    steps, one more GPU step is checked cell by cell on a sample of cells
+    (interior, wall-adjacent, lid-adjacent, edges) against the oracle's
+    C(S_bc(.)) evaluated on each cell's 3x3x3 neighbourhood."""
+    n = 256
+    mask = I.lid_driven_cavity_mask(n)
+    nu = 0.05 * (n - 2) / 1000.0
+    omega = X.xlb_omega_from_nu(nu)
+    lid = (1.0, (0.05, 0.0, 0.0))
+    c = Case(19, mask.shape, omega, "bgk", mask=mask, lid=lid)
+    sim = c.gpu_sim()
+    sim.step(30)
+    h_prev, k1 = sim.populations()
+    sim.step(1)
+    h_next, k2 = sim.populations()
+    assert k1 == 1 and k2 == 1
+    rng = np.random.default_rng(0)
+    pts = [tuple(rng.integers(1, n - 1, 3)) for _ in range(300)]
+    pts += [(z, y, x) for z in (1, n - 2) for y in (1, 2, n - 2) for x in (1, 5, n - 2)]
+    lat = c.lat
+    p = c.params()
+    w = lat.w[:, None, None, None]
+    worst = 0.0
+    for (z, y, x) in pts:
+        idx = np.ix_(range(z - 1, z + 2), range(y - 1, y + 2), range(x - 1, x + 2))
+        hp = h_prev[(slice(None),) + idx].astype(np.float64) + w
+        mp = mask[idx]
+        f = O.stream_bc(lat, hp, mp, p.bc)
+        hn = O.collide(lat, f, mp, p)[:, 1, 1, 1] - lat.w
+        g = h_next[:, z, y, x].astype(np.float64)
+        worst = max(worst, float(np.max(np.abs(g - hn))))
+    assert worst < 2e-7
+    sim.close()

@@ -405,10 +405,10 @@ def _adjoint_case(q, shape, steps, with_walls, force):
 
     def loss(r0):
         f = O.run(lat, O.init_state(lat, r0, u0, mask, p), mask, p, steps)
-        return O.kinetic_energy(lat, f, box)
+        return O.kinetic_energy(lat, f, mask, p, box)
 
-    def seed(fN):
-        return O.kinetic_energy_grads(lat, fN, box)
+    def seed(rho, u):
+        return O.kinetic_energy_grads(rho, u, box)
 
     drho, _ = O.gradient_init(lat, rho0, u0, mask, p, steps, seed)
     return lat, mask, rho0, loss, drho
