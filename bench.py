@@ -130,7 +130,7 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     assert stream.cuda_stream != 0
-    n = N_CAV
+    n = args.size
     cells = n ** 3
     sim, mask = _cavity_sim(torch, X, I, n, "f32", stream.cuda_stream)
     fluid = int((mask == 0).sum())
@@ -167,7 +167,7 @@ def run_ours(args, rank, world, dist):
     h_u = pin(np.zeros((3,) + mask.shape, np.float32))
     o_rho = torch.empty(mask.shape, dtype=torch.float32).pin_memory()
     o_u = torch.empty((3,) + mask.shape, dtype=torch.float32).pin_memory()
-    sim2 = X.Simulation(19, (n, n, n), cavity_omega(n), "bgk", "f32", stream=stream.cuda_stream)
+    sim2 = X.Simulation(19, (n, n, n), cavity_omega(n), "bgk", "f32", stream=stream.cuda_stream)  # noqa
     sim2.set_bc(X.XLB_CELL_LID, 1.0, (LID_U, 0.0, 0.0))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -397,6 +397,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--size", type=int, default=N_CAV,
+                    help="cavity edge (default 256, the benchmark workload; smaller only for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

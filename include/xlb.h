@@ -81,7 +81,8 @@ enum {
  * (XLB_ERR_UNSUPPORTED on D3Q19).  storage: XLB_STORE_*.  cuda_stream: a
  * cudaStream_t to queue work on, or NULL for a stream the library creates.
  * Every face is periodic until a mask is set.  Allocates two population
- * buffers of Q*N elements.  On failure *out is NULL. */
+ * buffers of Q*N elements.  A lattice holds at most 2^31 - 1 cells
+ * (XLB_ERR_UNSUPPORTED beyond).  On failure *out is NULL. */
 int xlb_create(xlb_ctx** out, int lattice, const int64_t dims[3], double omega, int collision, int storage,
                void* cuda_stream);
 

@@ -95,14 +95,14 @@ __device__ __forceinline__ void collide_vjp(const float (&df)[Q], const float (&
 }
 
 template <int Q>
-__device__ __forceinline__ long long dst_index(const Nbr& nb, int i) {
+__device__ __forceinline__ int dst_index(const Nbr& nb, int i) {
   return nb.xo[1 + Lattice<Q>::c(i, 0)] + nb.rb[1 + Lattice<Q>::c(i, 1)][1 + Lattice<Q>::c(i, 2)];
 }
 
 // hbar(x) = (S_bc^T abar)(x) for a fluid-like cell x.
 template <int Q>
 __device__ __forceinline__ void gather_adjoint(const float* __restrict__ ain, const StepParams& p, const Nbr& nb,
-                                               long long self, int slow, float (&hb)[Q]) {
+                                               int self, int slow, float (&hb)[Q]) {
   if (!slow) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) hb[i] = __ldg(ain + (long long)i * p.plane + dst_index<Q>(nb, i));
@@ -110,7 +110,7 @@ __device__ __forceinline__ void gather_adjoint(const float* __restrict__ ain, co
   }
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const long long d = dst_index<Q>(nb, i);
+    const int d = dst_index<Q>(nb, i);
     const int t = p.flags[d] & FLAG_TYPE;
     if (fluid_like(t))
       hb[i] = __ldg(ain + (long long)i * p.plane + d);
@@ -122,7 +122,7 @@ __device__ __forceinline__ void gather_adjoint(const float* __restrict__ ain, co
 }
 
 template <int Q, typename S>
-__device__ __forceinline__ void zero_out(float* aout, const StepParams& p, long long self) {
+__device__ __forceinline__ void zero_out(float* aout, const StepParams& p, int self) {
 #pragma unroll
   for (int i = 0; i < Q; ++i) aout[(long long)i * p.plane + self] = 0.f;
 }
@@ -130,7 +130,7 @@ __device__ __forceinline__ void zero_out(float* aout, const StepParams& p, long 
 // f_0 of a fluid-like cell exactly as the forward initialisation stored it:
 // f^eq(rho0, u0) rounded through the storage type.
 template <int Q, typename S>
-__device__ __forceinline__ void init_state(const float* rho0, const float* u0, long long ucs, long long self,
+__device__ __forceinline__ void init_state(const float* rho0, const float* u0, long long ucs, int self,
                                            float (&df)[Q], float& rho, float (&u)[3]) {
   rho = rho0[self];
   u[0] = u0[self];
@@ -160,10 +160,7 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_adjoint_step(const S* __restrict_
   Nbr nb;
   make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
   float df[Q], hb[Q], fb[Q];
-  if (fl & FLAG_SLOW)
-    pull_cell<Q, S>(hprev, p, c.x, c.y, c.z, c.self, fl & FLAG_TYPE, nb, df);
-  else
-    pull_periodic<Q, S>(hprev, p.plane, nb, df);
+  pull_cell<Q, S>(hprev, p, c.x, c.y, c.z, c.self, fl, nb, df);
   gather_adjoint<Q>(ain, p, nb, c.self, fl & FLAG_SLOW, hb);
   collide_vjp<Q, COLL>(df, hb, p, fb);
 #pragma unroll

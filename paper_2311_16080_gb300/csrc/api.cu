@@ -266,6 +266,8 @@ int xlb_create(xlb_ctx** out, int lattice, const int64_t dims[3], double omega, 
   if (lattice == 9 && nz != 1) return fail(nullptr, XLB_ERR_ARG, "D2Q9 needs nz = 1");
   if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30) || nx * ny > (1LL << 40) || nx * ny * nz > (1LL << 40))
     return fail(nullptr, XLB_ERR_ARG, "dims too large");
+  if (nx * ny * nz > 0x7fffffffLL)
+    return fail(nullptr, XLB_ERR_UNSUPPORTED, "at most 2^31 - 1 cells per lattice (32-bit cell indices)");
   if (!(omega > 0.0 && omega < 2.0)) return fail(nullptr, XLB_ERR_ARG, "omega must lie in (0, 2)");
   if (collision < 0 || collision > 2) return fail(nullptr, XLB_ERR_ARG, "unknown collision %d", collision);
   if (collision == XLB_COLL_KBC && lattice == 19)

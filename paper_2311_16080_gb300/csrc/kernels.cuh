@@ -17,44 +17,52 @@ constexpr int ROW_BLOCK = 128;
 
 struct CellIdx {
   int x, y, z;
-  long long self;
+  int self;
 };
 
 __device__ __forceinline__ bool cell_of_block(const StepParams& p, CellIdx& c) {
-  const int nxb = (p.nx + ROW_BLOCK - 1) / ROW_BLOCK;
-  const long long row = blockIdx.x / nxb;
-  const int xb = (int)(blockIdx.x - row * nxb);
-  c.x = xb * ROW_BLOCK + threadIdx.x;
+  const unsigned nxb = (unsigned)(p.nx + ROW_BLOCK - 1) / ROW_BLOCK;
+  const unsigned row = blockIdx.x / nxb;
+  const unsigned xb = blockIdx.x - row * nxb;
+  c.x = (int)(xb * ROW_BLOCK + threadIdx.x);
   if (c.x >= p.nx) return false;
-  c.y = (int)(row % p.ny);
-  c.z = (int)(row / p.ny);
-  c.self = (long long)c.x + (long long)p.nx * row;
+  c.y = (int)(row % (unsigned)p.ny);
+  c.z = (int)(row / (unsigned)p.ny);
+  c.self = c.x + p.nx * (int)row;
   return true;
 }
 
+// Blocks per SM the forward kernels are compiled for (register budget).
+template <int Q, int COLL>
+struct MinBlocks {
+  static constexpr int value = (COLL == 2) ? 4 : (Q == 27 ? 8 : (Q == 19 ? 9 : 12));
+};
+
 // Fused pull-stream + collide (+ body force): one lattice update per cell.
 // src holds post-collision populations h_{t-1}; dst receives h_t = C(S_bc(h_{t-1})).
-// Solid and EQ cells are skipped: no rule ever reads their stored values.
+// The periodic pull is issued before the cell's flag byte is known (no
+// dependent load in front of the 19/27 population loads); cells whose stencil
+// touches a boundary then patch the affected directions.  Solid and EQ cells
+// are computed but not stored: no rule ever reads their values.
 template <int Q, typename S, int COLL>
-__global__ void __launch_bounds__(ROW_BLOCK) k_stream_collide(const S* __restrict__ src, S* __restrict__ dst,
-                                                              const StepParams p) {
+__global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, COLL>::value)
+    k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, const StepParams p) {
   CellIdx c;
   if (!cell_of_block(p, c)) return;
-  int fl = 0;
-  if (p.has_mask) {
-    fl = p.flags[c.self];
-    if (!fluid_like(fl & FLAG_TYPE)) return;
-  }
+  const int fl = p.has_mask ? __ldg(p.flags + c.self) : 0;
   Nbr nb;
   make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
   float df[Q];
-  if (fl & FLAG_SLOW)
-    pull_cell<Q, S>(src, p, c.x, c.y, c.z, c.self, fl & FLAG_TYPE, nb, df);
-  else
-    pull_periodic<Q, S>(src, p.plane, nb, df);
+  pull_periodic<Q, S>(src, p.plane, nb, df);
+  if (fl & FLAG_SLOW) slow_rules<Q, S>(src, p, c.x, c.y, c.z, c.self, fl & FLAG_TYPE, nb, df);
   collide<Q, COLL>(df, p);
+  if (!fluid_like(fl & FLAG_TYPE)) return;
+  S* out = dst + c.self;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) Store<S>::st(dst + (long long)i * p.plane + c.self, df[i]);
+  for (int i = 0; i < Q; ++i) {
+    Store<S>::st(out, df[i]);
+    out += p.plane;
+  }
 }
 
 // Collision only, in place, on a state that holds post-stream populations
@@ -113,10 +121,7 @@ __device__ __forceinline__ void post_stream(const S* f, const StepParams& p, con
   if (kind_h) {
     Nbr nb;
     make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
-    if (fl & FLAG_SLOW)
-      pull_cell<Q, S>(f, p, c.x, c.y, c.z, c.self, fl & FLAG_TYPE, nb, df);
-    else
-      pull_periodic<Q, S>(f, p.plane, nb, df);
+    pull_cell<Q, S>(f, p, c.x, c.y, c.z, c.self, fl, nb, df);
   } else {
 #pragma unroll
     for (int i = 0; i < Q; ++i) df[i] = Store<S>::ld(f + (long long)i * p.plane + c.self);

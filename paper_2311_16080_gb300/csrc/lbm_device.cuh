@@ -16,10 +16,11 @@ enum Collision { COLL_NONE = 0, COLL_BGK = 1, COLL_KBC = 2 };
 
 // Periodic neighbour coordinates of one cell: xo[k] = x + k - 1 wrapped, and
 // rb[b][c] = row offset of (y + b - 1, z + c - 1) wrapped.  The source of
-// direction i is xo[1 - cx] + rb[1 - cy][1 - cz].
+// direction i is xo[1 - cx] + rb[1 - cy][1 - cz].  Cell indices are 32-bit
+// (the library caps a lattice at 2^31 - 1 cells); plane offsets are 64-bit.
 struct Nbr {
   int xo[3];
-  long long rb[3][3];
+  int rb[3][3];
 };
 
 __device__ __forceinline__ int wrap_m(int v, int n) { return v == 0 ? n - 1 : v - 1; }
@@ -34,11 +35,11 @@ __device__ __forceinline__ void make_nbr(Nbr& nb, int x, int y, int z, int nx, i
 #pragma unroll
   for (int b = 0; b < 3; ++b)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) nb.rb[b][c] = (long long)nx * ((long long)ys[b] + (long long)ny * zs[c]);
+    for (int c = 0; c < 3; ++c) nb.rb[b][c] = nx * (ys[b] + ny * zs[c]);
 }
 
 template <int Q>
-__device__ __forceinline__ long long src_index(const Nbr& nb, int i) {
+__device__ __forceinline__ int src_index(const Nbr& nb, int i) {
   return nb.xo[1 - Lattice<Q>::c(i, 0)] + nb.rb[1 - Lattice<Q>::c(i, 1)][1 - Lattice<Q>::c(i, 2)];
 }
 
@@ -46,28 +47,31 @@ __device__ __forceinline__ long long src_index(const Nbr& nb, int i) {
 template <int Q, typename S>
 __device__ __forceinline__ void pull_periodic(const S* __restrict__ src, long long plane, const Nbr& nb,
                                               float (&df)[Q]) {
-#pragma unroll
-  for (int i = 0; i < Q; ++i) df[i] = Store<S>::ld(src + (long long)i * plane + src_index<Q>(nb, i));
-}
-
-// Pull with the mask rules for a source cell x - c_i of type
-//   fluid-like: h_i(x - c_i);   WALL: h_opp(i)(x);
-//   LID: h_opp(i)(x) + 2 w_i rho_w (c_i . u_w) / cs^2;   EQ: f_i^eq(rho_w, u_w).
-template <int Q, typename S>
-__device__ __forceinline__ void pull_masked(const S* __restrict__ src, const StepParams& p, const Nbr& nb,
-                                            long long self, float (&df)[Q]) {
+  const S* base = src;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const long long s = src_index<Q>(nb, i);
-    const int t = p.flags[s] & FLAG_TYPE;
-    if (fluid_like(t)) {
-      df[i] = Store<S>::ld(src + (long long)i * p.plane + s);
-    } else if (t == EQ) {
-      df[i] = p.eq_df[i];
-    } else {
-      float v = Store<S>::ld(src + (long long)opposite<Q>(i) * p.plane + self);
-      if (t == LID) v += p.lid_term[i];
-      df[i] = v;
+    df[i] = Store<S>::ld(base + src_index<Q>(nb, i));
+    base += plane;
+  }
+}
+
+// Boundary rules applied on top of a periodic pull, for a source cell x - c_i
+// of type  fluid-like: keep h_i(x - c_i);   WALL: h_opp(i)(x);
+//   LID: h_opp(i)(x) + 2 w_i rho_w (c_i . u_w) / cs^2;   EQ: f_i^eq(rho_w, u_w).
+template <int Q, typename S>
+__device__ __forceinline__ void patch_masked(const S* __restrict__ src, const StepParams& p, const Nbr& nb,
+                                             int self, float (&df)[Q]) {
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int t = __ldg(p.flags + src_index<Q>(nb, i)) & FLAG_TYPE;
+    if (!fluid_like(t)) {
+      if (t == EQ) {
+        df[i] = p.eq_df[i];
+      } else {
+        float v = Store<S>::ld(src + (long long)opposite<Q>(i) * p.plane + self);
+        if (t == LID) v += p.lid_term[i];
+        df[i] = v;
+      }
     }
   }
 }
@@ -95,24 +99,33 @@ __device__ __forceinline__ void zou_he_inlet(const StepParams& p, float (&df)[Q]
   }
 }
 
-// Full post-stream populations of a fluid-like cell with every boundary rule:
-// mask substitution, then Zou-He on INLET cells, then the zero-gradient
-// outflow on OUTLET cells (c_x = -1 populations taken from the cell at x - 1).
+// The rules of a FLAG_SLOW cell on top of its periodic pull: mask
+// substitution, then Zou-He on INLET cells, then the zero-gradient outflow on
+// OUTLET cells (c_x = -1 populations taken from the pull at x - 1).
 template <int Q, typename S>
-__device__ __forceinline__ void pull_cell(const S* __restrict__ src, const StepParams& p, int x, int y, int z,
-                                          long long self, int type, const Nbr& nb, float (&df)[Q]) {
-  pull_masked<Q, S>(src, p, nb, self, df);
+__device__ __forceinline__ void slow_rules(const S* __restrict__ src, const StepParams& p, int x, int y, int z,
+                                        int self, int type, const Nbr& nb, float (&df)[Q]) {
+  patch_masked<Q, S>(src, p, nb, self, df);
   if (type == INLET) zou_he_inlet<Q>(p, df);
   if (type == OUTLET) {
     const int xl = wrap_m(x, p.nx);
     Nbr nl;
     make_nbr(nl, xl, y, z, p.nx, p.ny, p.nz);
     float dl[Q];
-    pull_masked<Q, S>(src, p, nl, self - x + xl, dl);
+    pull_periodic<Q, S>(src, p.plane, nl, dl);
+    patch_masked<Q, S>(src, p, nl, self - x + xl, dl);
 #pragma unroll
     for (int i = 0; i < Q; ++i)
       if (Lattice<Q>::c(i, 0) == -1) df[i] = dl[i];
   }
+}
+
+// Full post-stream populations of a fluid-like cell with every boundary rule.
+template <int Q, typename S>
+__device__ __forceinline__ void pull_cell(const S* __restrict__ src, const StepParams& p, int x, int y, int z,
+                                          int self, int fl, const Nbr& nb, float (&df)[Q]) {
+  pull_periodic<Q, S>(src, p.plane, nb, df);
+  if (fl & FLAG_SLOW) slow_rules<Q, S>(src, p, x, y, z, self, fl & FLAG_TYPE, nb, df);
 }
 
 template <int Q>
@@ -150,6 +163,20 @@ __device__ __forceinline__ void add_force(float (&df)[Q], float rho, const float
   for (int i = 0; i < Q; ++i) df[i] += weight<Q>(i) * rho * (eq_poly<Q>(i, v, vsq) - eq_poly<Q>(i, u, usq));
 }
 
+// KBC shear population ds_i from hd = D_aa / 2 (a = x, y, z) and
+// qo = Pi_ab / 4 (ab = xy, xz, yz); zero on the rest and corner directions.
+template <int Q>
+__device__ __forceinline__ float kbc_ds(int i, const float (&hd)[3], const float (&qo)[3]) {
+  const int cx = Lattice<Q>::c(i, 0), cy = Lattice<Q>::c(i, 1), cz = Lattice<Q>::c(i, 2);
+  if (nnz<Q>(i) == 1) return cx ? hd[0] : (cy ? hd[1] : hd[2]);
+  if (nnz<Q>(i) == 2) {
+    if (cx && cy) return (float)(cx * cy) * qo[0];
+    if (cx && cz) return (float)(cx * cz) * qo[1];
+    return (float)(cy * cz) * qo[2];
+  }
+  return 0.f;
+}
+
 // Collision C of Eq. 1 on one fluid-like cell, in place on deviations.
 //   BGK (Eq. 3): df_i += omega (df_i^eq - df_i)
 //   KBC (Karlin, Bosch, Chikatamarla 2014): f^neq = ds + dh, beta = omega / 2,
@@ -182,53 +209,45 @@ __device__ __forceinline__ void collide(float (&df)[Q], const StepParams& p) {
       df[i] = fmaf(p.omega, dfeq - df[i], df[i]);
     }
   } else {
-    // KBC: non-equilibrium part and its second moments
-    float fneq[Q], feq[Q];
+    // KBC.  Only f^neq stays live; the equilibrium terms and ds are cheap to
+    // recompute.  With dh = f^neq - ds the update reads
+    //   df_i <- df_i^eq + (1 - beta gamma) f^neq_i - beta (2 - gamma) ds_i.
+    float fneq[Q];
+    float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx yy zz xy xz yz
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const float poly = eq_poly<Q>(i, u, usq);
-      const float dfeq = weight<Q>(i) * (drho + rho * poly);
-      fneq[i] = df[i] - dfeq;
-      feq[i] = weight<Q>(i) * rho * (1.0f + poly);
-    }
-    float P[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = a; b < 3; ++b)
-          if (Lattice<Q>::c(i, a) * Lattice<Q>::c(i, b) != 0)
-            P[a][b] += (float)(Lattice<Q>::c(i, a) * Lattice<Q>::c(i, b)) * fneq[i];
+      const float fn = df[i] - weight<Q>(i) * (drho + rho * eq_poly<Q>(i, u, usq));
+      fneq[i] = fn;
+      if (Lattice<Q>::c(i, 0)) P[0] += fn;
+      if (Lattice<Q>::c(i, 1)) P[1] += fn;
+      if (Lattice<Q>::c(i, 2)) P[2] += fn;
+      if (Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 1)) P[3] += (float)(Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 1)) * fn;
+      if (Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 2)) P[4] += (float)(Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 2)) * fn;
+      if (Lattice<Q>::c(i, 1) * Lattice<Q>::c(i, 2)) P[5] += (float)(Lattice<Q>::c(i, 1) * Lattice<Q>::c(i, 2)) * fn;
     }
     constexpr float inv_d = 1.0f / Lattice<Q>::D;
-    const float tr = P[0][0] + P[1][1] + P[2][2];
+    const float tr = P[0] + P[1] + P[2];
+    // ds_i: D_aa / 2 on the axis directions, c_a c_b Pi_ab / 4 on the two-component ones
+    const float hd[3] = {0.5f * (P[0] - tr * inv_d), 0.5f * (P[1] - tr * inv_d), 0.5f * (P[2] - tr * inv_d)};
+    const float qo[3] = {0.25f * P[3], 0.25f * P[4], 0.25f * P[5]};
     float sh = 0.f, hh = 0.f;
-    float ds[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      float s = 0.f;
-      if (nnz<Q>(i) == 1) {
-        const int a = Lattice<Q>::c(i, 0) ? 0 : (Lattice<Q>::c(i, 1) ? 1 : 2);
-        s = 0.5f * (P[a][a] - tr * inv_d);
-      } else if (nnz<Q>(i) == 2) {
-        const int a = Lattice<Q>::c(i, 0) ? 0 : 1;
-        const int b = Lattice<Q>::c(i, 2) ? 2 : 1;
-        s = 0.25f * (float)(Lattice<Q>::c(i, a) * Lattice<Q>::c(i, b)) * P[a][b];
-      }
-      ds[i] = s;
+      const float s = kbc_ds<Q>(i, hd, qo);
       const float dh = fneq[i] - s;
-      const float ife = 1.0f / feq[i];
-      sh = fmaf(s * dh, ife, sh);
-      hh = fmaf(dh * dh, ife, hh);
+      // <a|b> weight 1 / f_i^eq, f_i^eq = w_i rho (1 + poly_i); the common 1/rho cancels in gamma
+      const float iw = __fdividef(1.0f / weight<Q>(i), 1.0f + eq_poly<Q>(i, u, usq));
+      sh = fmaf(s * dh, iw, sh);
+      hh = fmaf(dh * dh, iw, hh);
     }
     const float beta = 0.5f * p.omega;
     const float ib = 1.0f / beta;
-    const float gamma = (hh < 1e-20f) ? 2.0f : ib - (2.0f - ib) * sh / hh;
+    const float gamma = (hh < 1e-20f * rho) ? 2.0f : ib - (2.0f - ib) * sh / hh;
+    const float a1 = 1.0f - beta * gamma, a2 = beta * (2.0f - gamma);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const float dh = fneq[i] - ds[i];
-      df[i] -= beta * (2.0f * ds[i] + gamma * dh);
+      const float dfeq = weight<Q>(i) * (drho + rho * eq_poly<Q>(i, u, usq));
+      df[i] = dfeq + a1 * fneq[i] - a2 * kbc_ds<Q>(i, hd, qo);
     }
   }
   if (p.has_force) add_force<Q>(df, rho, force_u, usq, p.F);
