@@ -100,8 +100,19 @@ const char* xlb_status_string(int status);
 double xlb_omega_from_nu(double nu);
 
 /* Set the per-cell type mask (uint8 codes XLB_CELL_*, N cells, x fastest).
- * Codes >= 6 give XLB_ERR_ARG and leave the previous mask in place. */
+ * Codes >= 6 give XLB_ERR_ARG and leave the previous mask in place.  Between
+ * steps, a new mask (like new boundary values from xlb_set_bc) acts from the
+ * next step on: the current state keeps the boundaries it was streamed with.
+ * XLB_ERR_STATE while a tape is open. */
 int xlb_set_mask(xlb_ctx* ctx, const uint8_t* mask);
+
+/* Sizes of the boundary tables of the current mask: n_links = number of
+ * (fluid cell, direction) pairs whose source cell is WALL, LID or EQ; n_fix
+ * = number of INLET and OUTLET cells.  After each update a boundary pass
+ * writes, for every link, the value the rule prescribes into the source
+ * cell's slot for that direction (a ghost value, so the next update can pull
+ * every cell as if periodic) and recomputes the inlet / outlet cells. */
+int xlb_boundary_links(const xlb_ctx* ctx, int64_t* n_links, int64_t* n_fix);
 
 /* Prescribed state of a boundary type: XLB_CELL_LID (rho_w, u_w of the
  * moving wall), XLB_CELL_INLET (Zou-He velocity u; rho ignored) or
@@ -138,7 +149,9 @@ int xlb_macroscopic(xlb_ctx* ctx, float* rho, float* u);
  * shift).  Host outputs; synchronises. */
 int xlb_reduce(xlb_ctx* ctx, double out_mass[1], double out_mom[3]);
 
-/* Wait for all work queued on the ctx's stream. */
+/* Wait for all work queued on the ctx's stream; XLB_ERR_TIMEOUT if a bounded
+ * wait inside a kernel expired since the last check (the results of those
+ * steps are invalid). */
 int xlb_synchronize(xlb_ctx* ctx);
 
 /* ---- checkpoint / resume (Section 3.7) --------------------------------- */
@@ -182,6 +195,23 @@ int xlb_adjoint_init_grad(xlb_ctx* ctx, float* dL_drho0, float* dL_du0);
 
 /* Free the tape, checkpoints and adjoint buffers. */
 int xlb_tape_end(xlb_ctx* ctx);
+
+/* ---- kernel selection -------------------------------------------------- */
+
+/* Variants of the bulk pass of an update (same arithmetic):
+ *   XLB_KERNEL_DIRECT: one thread per cell, populations loaded straight from
+ *     global memory;
+ *   XLB_KERNEL_VEC:    4 consecutive cells per thread, one aligned 4-wide load
+ *     per direction, the +-x neighbour element exchanged by warp shuffles
+ *     (16-bit storage, D2Q9 / D3Q19, BGK / NONE, nx % 4 == 0);
+ *   XLB_KERNEL_AUTO:   VEC where possible, else DIRECT (the default). */
+enum { XLB_KERNEL_AUTO = 0, XLB_KERNEL_DIRECT = 1, XLB_KERNEL_VEC = 2 };
+
+/* Choose the variant (XLB_ERR_UNSUPPORTED if it cannot run this ctx). */
+int xlb_set_kernel(xlb_ctx* ctx, int variant);
+
+/* The variant the next update launches (DIRECT or VEC). */
+int xlb_get_kernel(const xlb_ctx* ctx, int* variant);
 
 /* ---- timing of the hot kernels ----------------------------------------- */
 

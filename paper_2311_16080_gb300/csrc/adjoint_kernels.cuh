@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_adjoint_step(const S* __restrict_
   Nbr nb;
   make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
   float df[Q], hb[Q], fb[Q];
-  pull_cell<Q, S>(hprev, p, c.x, c.y, c.z, c.self, fl, nb, df);
+  pull_cell<Q, S>(hprev, p, c.x, c.y, c.z, fl & FLAG_TYPE, nb, df);
   gather_adjoint<Q>(ain, p, nb, c.self, fl & FLAG_SLOW, hb);
   collide_vjp<Q, COLL>(df, hb, p, fb);
 #pragma unroll

@@ -15,6 +15,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -41,6 +42,10 @@ struct xlb_ctx {
   int cur = 0;
   uint8_t* flags = nullptr;
   bool has_mask = false;
+  int2* links = nullptr;  // ghost links {cell, dir | type << 8} of the mask
+  long long n_links = 0;
+  int* fix = nullptr;  // inlet / outlet cells (recomputed after a bulk pass)
+  long long n_fix = 0;
   bool has_inlet_outlet = false;
   float* init_fields = nullptr;  // (1 + D) * N: rho0, u0 (component-major)
   bool has_init = false;
@@ -68,6 +73,8 @@ struct xlb_ctx {
   float* abar[2] = {nullptr, nullptr};
   int acur = 0;
   int64_t adj_t = -1;  // time index of the adjoint held in abar[acur]
+  // kernel variant of the bulk pass (XLB_KERNEL_*)
+  int variant = 0;
   // profiling
   bool prof = false;
   std::vector<EventPair> ev_pool;
@@ -146,6 +153,7 @@ static StepParams make_params(const xlb_ctx* c) {
     p.inlet_u[2] = 0.f;
   }
   p.eq_rho = c->eq_rho;
+  p.err = c->err_word ? c->err_word + 1 : nullptr;
   // constant boundary terms per direction, in double then rounded once
   auto fill = [&](auto lat_tag) {
     constexpr int Q = decltype(lat_tag)::value;
@@ -211,21 +219,86 @@ static void prof_end(xlb_ctx* c, cudaEvent_t* b) {
   if (b) cudaEventRecord(*b, c->stream);
 }
 
-// One fused step from buffer src to dst (either the live pair or tape slots).
+// The vectorised bulk kernel (4 cells per thread) runs 16-bit storage with
+// BGK or NONE collision on D2Q9 / D3Q19 when nx is a multiple of 4; FP32 is
+// fastest with one cell per thread (measured on the 256^3 cavity).
+static bool vec_possible(const xlb_ctx* c) {
+  return c->esize == 2 && c->Q != 27 && c->coll != XLB_COLL_KBC && c->nx % 4 == 0;
+}
+
+static bool use_vec(const xlb_ctx* c) {
+  if (c->variant == XLB_KERNEL_DIRECT) return false;
+  return vec_possible(c);
+}
+
+// Boundary pass on dst after a pass that produced post-collision values
+// there: ghost values of every link and of the inlet / outlet cells' links;
+// with `fix_src`, the inlet / outlet cells are first recomputed from it.
+static int boundary_pass(xlb_ctx* c, const void* fix_src, void* dst) {
+  if (!c->has_mask || c->n_links + c->n_fix == 0) return XLB_OK;
+  LaunchArgs a = base_args(c);
+  a.src = fix_src ? fix_src : dst;
+  a.dst = dst;
+  a.links = c->links;
+  a.n_links = c->n_links;
+  a.fix = c->fix;
+  a.n_fix = c->n_fix;
+  a.recompute = fix_src ? 1 : 0;
+  return dispatch(c, OP_BOUNDARY, a);
+}
+
+// One lattice update from buffer src to dst (either the live pair or tape
+// slots): a bulk pass that pulls every cell as if periodic (no flag reads) --
+// the wall, lid and EQ cells hold ghost values that make that pull exact --
+// then the boundary pass, which rewrites the ghosts for the next step and
+// recomputes the inlet / outlet cells.
 static int launch_step(xlb_ctx* c, const void* src, void* dst) {
+  const bool vec = use_vec(c);
   LaunchArgs a = base_args(c);
   a.src = src;
   a.dst = dst;
+  a.p.has_mask = 0;  // bulk pass: every cell pulled as if periodic
   cudaEvent_t* pe = prof_begin(c, 0);
-  int r = dispatch(c, OP_STEP, a);
+  int r = dispatch(c, vec ? OP_STEP_VEC : OP_STEP, a);
+  if (!r) r = boundary_pass(c, src, dst);
   prof_end(c, pe);
   return r;
+}
+
+// Device error word (bounded waits that expired) -> XLB_ERR_TIMEOUT.
+static int check_device_error(xlb_ctx* c) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, c->err_word + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (h) {
+    CK(cudaMemsetAsync(c->err_word + 1, 0, sizeof(int), c->stream));
+    return fail(c, XLB_ERR_TIMEOUT, "a bounded wait inside a kernel expired (device error %d); results are invalid", h);
+  }
+  return XLB_OK;
+}
+
+// Turn a post-collision state h_{t-1} into the post-stream state f_t it
+// represents, under the current boundaries (a stream-only update into the
+// other buffer).  Used before the boundaries change, so that f_t keeps the
+// boundaries it was streamed with and the change acts from step t + 1 on.
+static int materialize_post_stream(xlb_ctx* c) {
+  if (!c->kind_h) return XLB_OK;
+  const int coll = c->coll;
+  c->coll = XLB_COLL_NONE;
+  const int r = launch_step(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
+  c->coll = coll;
+  if (r) return r;
+  c->cur ^= 1;
+  c->kind_h = 0;
+  return XLB_OK;
 }
 
 static int launch_collide_local(xlb_ctx* c, void* buf) {
   LaunchArgs a = base_args(c);
   a.dst = buf;
-  return dispatch(c, OP_COLLIDE_LOCAL, a);
+  int r = dispatch(c, OP_COLLIDE_LOCAL, a);
+  if (!r) r = boundary_pass(c, nullptr, buf);  // ghosts of the first post-collision state
+  return r;
 }
 
 static int launch_init(xlb_ctx* c, void* dst) {
@@ -313,6 +386,8 @@ int xlb_create(xlb_ctx** out, int lattice, const int64_t dims[3], double omega, 
   e = cudaMalloc(&c->red_out, 4 * sizeof(double) + sizeof(int) * 4);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(reduction)"));
   c->err_word = (int*)(c->red_out + 4);
+  e = cudaMemset(c->err_word, 0, 4 * sizeof(int));
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemset(error words)"));
   e = cudaMalloc(&c->init_fields, sizeof(float) * (size_t)(1 + c->D) * (size_t)c->N);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(init fields)"));
   *out = c;
@@ -328,6 +403,8 @@ void xlb_destroy(xlb_ctx* c) {
   for (int k = 0; k < 2; ++k)
     if (c->buf[k]) cudaFree(c->buf[k]);
   if (c->flags) cudaFree(c->flags);
+  if (c->links) cudaFree(c->links);
+  if (c->fix) cudaFree(c->fix);
   if (c->init_fields) cudaFree(c->init_fields);
   if (c->partial) cudaFree(c->partial);
   if (c->red_out) cudaFree(c->red_out);
@@ -343,6 +420,7 @@ void xlb_destroy(xlb_ctx* c) {
 int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
   if (!c) return XLB_ERR_ARG;
   if (!mask) return fail(c, XLB_ERR_ARG, "mask is null");
+  if (c->tape_open) return fail(c, XLB_ERR_STATE, "the mask cannot change while a tape is open");
   const size_t n = (size_t)c->N;
   uint8_t* dmask = nullptr;
   bool host_mask = !is_device_ptr(mask);
@@ -381,27 +459,93 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
     for (size_t k = 0; k < n && !io; ++k) io = (hp[k] == XLB_CELL_INLET || hp[k] == XLB_CELL_OUTLET);
     c->has_inlet_outlet = io;
   }
+  // boundary tables: ghost links and inlet / outlet cells
+  int2* nlinks = nullptr;
+  int* nfix = nullptr;
+  long long nl = 0, nfx = 0;
+  {
+    const long long nb = bnd_list_blocks(c->N);
+    int* counts = nullptr;
+    long long* offs = nullptr;
+    cudaError_t e = cudaMalloc(&counts, sizeof(int) * 2 * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&offs, sizeof(long long) * 2 * nb);
+    std::vector<int> hc(2 * nb);
+    std::vector<long long> ho(2 * nb);
+    if (e == cudaSuccess && launch_bnd_count(c->Q, nf, (int)c->nx, (int)c->ny, (int)c->nz, counts, c->stream) != 0)
+      e = cudaErrorInvalidValue;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hc.data(), counts, sizeof(int) * 2 * nb, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) {
+      for (long long b = 0; b < nb; ++b) {
+        ho[2 * b] = nl;
+        ho[2 * b + 1] = nfx;
+        nl += hc[2 * b];
+        nfx += hc[2 * b + 1];
+      }
+      e = cudaMemcpyAsync(offs, ho.data(), sizeof(long long) * 2 * nb, cudaMemcpyHostToDevice, c->stream);
+    }
+    if (e == cudaSuccess && nl > 0) e = cudaMalloc(&nlinks, sizeof(int2) * nl);
+    if (e == cudaSuccess && nfx > 0) e = cudaMalloc(&nfix, sizeof(int) * nfx);
+    if (e == cudaSuccess && (nl > 0 || nfx > 0) &&
+        launch_bnd_write(c->Q, nf, (int)c->nx, (int)c->ny, (int)c->nz, offs, nlinks, nfix, c->stream) != 0)
+      e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (counts) cudaFree(counts);
+    if (offs) cudaFree(offs);
+    if (e != cudaSuccess) {
+      cudaFree(nf);
+      if (nlinks) cudaFree(nlinks);
+      if (nfix) cudaFree(nfix);
+      return cuda_fail(c, e, "boundary tables");
+    }
+  }
+  {
+    const int r = materialize_post_stream(c);  // f_t under the old mask
+    if (r) {
+      cudaFree(nf);
+      if (nlinks) cudaFree(nlinks);
+      if (nfix) cudaFree(nfix);
+      return r;
+    }
+  }
   if (c->flags) cudaFree(c->flags);
+  if (c->links) cudaFree(c->links);
+  if (c->fix) cudaFree(c->fix);
   c->flags = nf;
+  c->links = nlinks;
+  c->n_links = nl;
+  c->fix = nfix;
+  c->n_fix = nfx;
   c->has_mask = true;
+  return XLB_OK;
+}
+
+int xlb_boundary_links(const xlb_ctx* c, int64_t* n_links, int64_t* n_fix) {
+  if (!c || !n_links || !n_fix) return XLB_ERR_ARG;
+  *n_links = c->n_links;
+  *n_fix = c->n_fix;
   return XLB_OK;
 }
 
 int xlb_set_bc(xlb_ctx* c, int type, float rho, const float u[3]) {
   if (!c) return XLB_ERR_ARG;
   if (!u) return fail(c, XLB_ERR_ARG, "u is null");
+  if (type != XLB_CELL_LID && type != XLB_CELL_INLET && type != XLB_CELL_EQ)
+    return fail(c, XLB_ERR_ARG, "cell type %d carries no boundary value", type);
+  if (type == XLB_CELL_INLET && !(u[0] < 1.0f)) return fail(c, XLB_ERR_ARG, "inlet u_x must be < 1");
+  if (type == XLB_CELL_EQ && !(rho > 0.f)) return fail(c, XLB_ERR_ARG, "EQ density must be > 0");
+  if (c->tape_open) return fail(c, XLB_ERR_STATE, "boundary values cannot change while a tape is open");
+  const int r = materialize_post_stream(c);  // f_t with the old values
+  if (r) return r;
   if (type == XLB_CELL_LID) {
     c->lid_rho = rho;
     for (int a = 0; a < 3; ++a) c->lid_u[a] = u[a];
   } else if (type == XLB_CELL_INLET) {
-    if (!(u[0] < 1.0f)) return fail(c, XLB_ERR_ARG, "inlet u_x must be < 1");
     for (int a = 0; a < 3; ++a) c->inlet_u[a] = u[a];
-  } else if (type == XLB_CELL_EQ) {
-    if (!(rho > 0.f)) return fail(c, XLB_ERR_ARG, "EQ density must be > 0");
+  } else {
     c->eq_rho = rho;
     for (int a = 0; a < 3; ++a) c->eq_u[a] = u[a];
-  } else {
-    return fail(c, XLB_ERR_ARG, "cell type %d carries no boundary value", type);
   }
   return XLB_OK;
 }
@@ -409,6 +553,7 @@ int xlb_set_bc(xlb_ctx* c, int type, float rho, const float u[3]) {
 int xlb_set_force(xlb_ctx* c, const float F[3]) {
   if (!c) return XLB_ERR_ARG;
   if (!F) return fail(c, XLB_ERR_ARG, "F is null");
+  if (c->tape_open) return fail(c, XLB_ERR_STATE, "the force cannot change while a tape is open");
   for (int a = 0; a < 3; ++a) c->F[a] = (a < c->D) ? F[a] : 0.f;
   c->has_force = (c->F[0] != 0.f || c->F[1] != 0.f || c->F[2] != 0.f);
   return XLB_OK;
@@ -484,6 +629,23 @@ int xlb_get_time(const xlb_ctx* c, int64_t* t) {
 int xlb_synchronize(xlb_ctx* c) {
   if (!c) return XLB_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));
+  return check_device_error(c);
+}
+
+int xlb_set_kernel(xlb_ctx* c, int variant) {
+  if (!c) return XLB_ERR_ARG;
+  if (variant < XLB_KERNEL_AUTO || variant > XLB_KERNEL_VEC)
+    return fail(c, XLB_ERR_ARG, "unknown kernel variant %d", variant);
+  if (variant == XLB_KERNEL_VEC && !vec_possible(c))
+    return fail(c, XLB_ERR_UNSUPPORTED,
+                "the vectorised kernel needs 16-bit storage, D2Q9 or D3Q19, BGK/NONE and nx %% 4 == 0");
+  c->variant = variant;
+  return XLB_OK;
+}
+
+int xlb_get_kernel(const xlb_ctx* c, int* variant) {
+  if (!c || !variant) return XLB_ERR_ARG;
+  *variant = use_vec(c) ? XLB_KERNEL_VEC : XLB_KERNEL_DIRECT;
   return XLB_OK;
 }
 
@@ -507,6 +669,8 @@ int xlb_macroscopic(xlb_ctx* c, float* rho, float* u) {
   a.u_out = du;
   int r = dispatch(c, OP_MACRO, a);
   if (r) return r;
+  r = check_device_error(c);
+  if (r) return r;
   if (host) {
     if (rho) CK(cudaMemcpyAsync(rho, dr, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     if (u) CK(cudaMemcpyAsync(u, du, (size_t)c->D * n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
@@ -526,7 +690,8 @@ int xlb_reduce(xlb_ctx* c, double out_mass[1], double out_mom[3]) {
   launch_reduce_final(c->partial, row_blocks(a.p), c->red_out, c->stream);
   double h[4];
   CK(cudaMemcpyAsync(h, c->red_out, sizeof h, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  r = check_device_error(c);
+  if (r) return r;
   if (out_mass) out_mass[0] = h[0];
   if (out_mom)
     for (int k = 0; k < 3; ++k) out_mom[k] = h[1 + k];
@@ -586,6 +751,7 @@ int xlb_state_set(xlb_ctx* c, const void* buf, size_t bytes) {
   c->t = h.t;
   c->kind_h = h.kind_h ? 1 : 0;
   c->has_init = true;
+  if (c->kind_h) return boundary_pass(c, nullptr, c->buf[c->cur]);  // ghosts of the restored state
   return XLB_OK;
 }
 

@@ -1,0 +1,6 @@
+// KBC kernels instantiated for Q = 27, f16 storage.
+#include "kernels.cuh"
+
+namespace xlb {
+int launch_fwd_q27_s1_kbc(Op op, const LaunchArgs& a) { return launch_typed<27, __half, COLL_KBC>(op, a); }
+}  // namespace xlb

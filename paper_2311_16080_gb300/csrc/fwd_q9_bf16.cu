@@ -1,6 +1,11 @@
-// Forward kernels instantiated for Q = 9, bf16 storage.
+// Forward kernels instantiated for Q = 9, bf16 storage, NONE and BGK
+// collisions, plus the collision-independent kernels.
 #include "kernels.cuh"
 
 namespace xlb {
-int launch_fwd_q9_s2(Op op, const LaunchArgs& a) { return launch_typed<9, __nv_bfloat16>(op, a); }
+int launch_fwd_q9_s2(Op op, const LaunchArgs& a) {
+  if (a.coll == COLL_NONE && (op == OP_STEP || op == OP_STEP_VEC || op == OP_BOUNDARY || op == OP_COLLIDE_LOCAL))
+    return launch_typed<9, __nv_bfloat16, COLL_NONE>(op, a);
+  return launch_typed<9, __nv_bfloat16, COLL_BGK>(op, a);
+}
 }  // namespace xlb

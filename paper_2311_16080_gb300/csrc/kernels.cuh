@@ -8,8 +8,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
-#include "lbm_device.cuh"
 #include "launch.h"
+#include "lbm_device.cuh"
 
 namespace xlb {
 
@@ -38,29 +38,194 @@ struct MinBlocks {
   static constexpr int value = (COLL == 2) ? 4 : (Q == 27 ? 8 : (Q == 19 ? 9 : 12));
 };
 
-// Fused pull-stream + collide (+ body force): one lattice update per cell.
-// src holds post-collision populations h_{t-1}; dst receives h_t = C(S_bc(h_{t-1})).
-// The periodic pull is issued before the cell's flag byte is known (no
-// dependent load in front of the 19/27 population loads); cells whose stencil
-// touches a boundary then patch the affected directions.  Solid and EQ cells
-// are computed but not stored: no rule ever reads their values.
+// Bulk pass of an update, one thread per cell: pull-stream + collide
+// (+ body force) of every cell as if periodic.  src holds post-collision
+// populations h_{t-1} with ghost values in the boundary cells, so the pull is
+// exact for every fluid cell; dst receives h_t = C(S_bc(h_{t-1})).  Boundary
+// cells get values nobody reads until k_boundary rewrites them; inlet /
+// outlet cells are recomputed there too.
 template <int Q, typename S, int COLL>
 __global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, COLL>::value)
     k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, const StepParams p) {
   CellIdx c;
   if (!cell_of_block(p, c)) return;
-  const int fl = p.has_mask ? __ldg(p.flags + c.self) : 0;
   Nbr nb;
   make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
   float df[Q];
   pull_periodic<Q, S>(src, p.plane, nb, df);
-  if (fl & FLAG_SLOW) slow_rules<Q, S>(src, p, c.x, c.y, c.z, c.self, fl & FLAG_TYPE, nb, df);
   collide<Q, COLL>(df, p);
-  if (!fluid_like(fl & FLAG_TYPE)) return;
   S* out = dst + c.self;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     Store<S>::st(out, df[i]);
+    out += p.plane;
+  }
+}
+
+// Ghost value of the link (cell x, direction i) whose source w = x - c_i has
+// type t: what the boundary rule gives f_i(x) at the next update.
+//   WALL: h_opp(i)(x);  LID: h_opp(i)(x) + 2 w_i rho_w (c_i . u_w) / cs^2;
+//   EQ: f_i^eq(rho_w, u_w).
+// (w, i) determines x, so no two links write the same slot.
+template <int Q, typename S>
+__device__ __forceinline__ void write_ghost(S* __restrict__ dst, const StepParams& p, int x, int y, int z, int i,
+                                            int t, float h_opp) {
+  int dx = 0, dy = 0, dz = 0;
+  float add = 0.f, eqv = 0.f;
+#pragma unroll
+  for (int j = 1; j < Q; ++j)
+    if (j == i) {
+      dx = Lattice<Q>::c(j, 0);
+      dy = Lattice<Q>::c(j, 1);
+      dz = Lattice<Q>::c(j, 2);
+      add = p.lid_term[j];
+      eqv = p.eq_df[j];
+    }
+  int wx = x - dx, wy = y - dy, wz = z - dz;
+  wx = wx < 0 ? p.nx - 1 : (wx >= p.nx ? 0 : wx);
+  wy = wy < 0 ? p.ny - 1 : (wy >= p.ny ? 0 : wy);
+  wz = wz < 0 ? p.nz - 1 : (wz >= p.nz ? 0 : wz);
+  const float v = t == EQ ? eqv : (t == LID ? h_opp + add : h_opp);
+  Store<S>::st(dst + (long long)i * p.plane + (wx + p.nx * (wy + p.ny * wz)), v);
+}
+
+// Boundary pass on dst, after a pass that wrote post-collision values there.
+// Threads [0, n_links) write the ghost values of the links of FLUID cells
+// (the link list).  Threads [n_links, n_links + n_fix) handle one INLET or
+// OUTLET cell each: with `recompute`, its update from src with the full
+// rules (the bulk pass pulled it as if periodic); then the ghosts of its own
+// links.  src is read only by the recomputation, which needs the ghosts of
+// the previous state, already in src.
+template <int Q, typename S, int COLL>
+__global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ src, S* __restrict__ dst,
+                                                        const StepParams p, const int2* __restrict__ links,
+                                                        int n_links, const int* __restrict__ fix, int n_fix,
+                                                        int recompute) {
+  const int k = blockIdx.x * ROW_BLOCK + threadIdx.x;
+  if (k < n_links) {
+    const int2 l = __ldg(links + k);
+    const int x = l.x, i = l.y & 0xff, t = l.y >> 8;
+    const int cx = x % p.nx, r = x / p.nx;
+    int io = 0;
+#pragma unroll
+    for (int j = 1; j < Q; ++j)
+      if (j == i) io = opposite<Q>(j);
+    const float h = t == EQ ? 0.f : Store<S>::ld_plain(dst + (long long)io * p.plane + x);
+    write_ghost<Q, S>(dst, p, cx, r % p.ny, r / p.ny, i, t, h);
+    return;
+  }
+  const int kf = k - n_links;
+  if (kf >= n_fix) return;
+  const int self = __ldg(fix + kf);
+  const int x = self % p.nx;
+  const int r = self / p.nx;
+  const int y = r % p.ny, z = r / p.ny;
+  Nbr nb;
+  make_nbr(nb, x, y, z, p.nx, p.ny, p.nz);
+  float df[Q];
+  if (recompute) {
+    pull_cell<Q, S>(src, p, x, y, z, __ldg(p.flags + self) & FLAG_TYPE, nb, df);
+    collide<Q, COLL>(df, p);
+    S* out = dst + self;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      Store<S>::st(out, df[i]);
+      out += p.plane;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) df[i] = Store<S>::ld_plain(dst + (long long)i * p.plane + self);
+  }
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int t = __ldg(p.flags + src_index<Q>(nb, i)) & FLAG_TYPE;
+    if (!fluid_like(t)) {
+      // the stored (rounded) value, as the link threads read it
+      S hs;
+      Store<S>::st(&hs, df[opposite<Q>(i)]);
+      write_ghost<Q, S>(dst, p, x, y, z, i, t, Store<S>::ld_plain(&hs));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Vectorised direct kernel.  Each thread owns V consecutive cells of one row
+// (x0 = V * slot); a warp covers 32 V consecutive cells and never straddles a
+// row.  Every direction is one aligned V-wide load of the source row at x0;
+// the pull's x shift by c_x = +-1 takes the missing end element from the
+// neighbouring lane with a warp shuffle, and only the lane at the warp's (or
+// row's) edge loads it from memory, with the periodic wrap.  Like the one-cell
+// kernel it is a bulk pass (ghost values make the pull exact).  Stores are
+// V-wide.  Needs nx % V == 0.
+
+template <int Q, typename S, int COLL, int V>
+struct VecMinBlocks {
+  static constexpr int value = (COLL == 2) ? 2 : (Q * V > 64 ? 3 : 4);
+};
+
+template <int Q, typename S, int COLL, int V>
+__global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
+    k_sc_vec(const S* __restrict__ src, S* __restrict__ dst, const StepParams p) {
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const int spr = (nx / V + 31) / 32 * 32;  // slots per row, whole warps
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = (int)(t / spr);
+  if (row >= ny * nz) return;  // whole warps only
+  const int slot = (int)(t - (long long)row * spr);
+  const int lane = threadIdx.x & 31;
+  const bool active = slot * V < nx;
+  const int x0 = active ? slot * V : nx - V;
+  const int y = row % ny, z = row / ny;
+  const bool last = !active || x0 + V >= nx;  // no active right neighbour lane
+  const int xm = x0 == 0 ? nx - 1 : x0 - 1;    // element left of the vector
+  const int xp = x0 + V >= nx ? 0 : x0 + V;    // element right of the vector
+  int rb[3][3];
+  {
+    const int ys[3] = {wrap_m(y, ny), y, wrap_p(y, ny)};
+    const int zs[3] = {nz > 1 ? wrap_m(z, nz) : 0, z, nz > 1 ? wrap_p(z, nz) : 0};
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) rb[b][c] = nx * (ys[b] + ny * zs[c]);
+  }
+  float v[Q][V];
+  const S* base = src;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = Lattice<Q>::c(i, 0);
+    const S* r = base + rb[1 - Lattice<Q>::c(i, 1)][1 - Lattice<Q>::c(i, 2)];
+    float w[V];
+    VecIO<S, V>::ld(r + x0, w);
+    if (cx == 0) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) v[i][k] = w[k];
+    } else if (cx == 1) {  // pull from x - 1
+      const float up = __shfl_up_sync(0xffffffffu, w[V - 1], 1);
+      v[i][0] = lane > 0 ? up : Store<S>::ld(r + xm);
+#pragma unroll
+      for (int k = 1; k < V; ++k) v[i][k] = w[k - 1];
+    } else {  // pull from x + 1
+      const float dn = __shfl_down_sync(0xffffffffu, w[0], 1);
+      v[i][V - 1] = (lane < 31 && !last) ? dn : Store<S>::ld(r + xp);
+#pragma unroll
+      for (int k = 0; k < V - 1; ++k) v[i][k] = w[k + 1];
+    }
+    base += p.plane;
+  }
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    float d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = v[i][k];
+    collide<Q, COLL>(d, p);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i][k] = d[i];
+  }
+  if (!active) return;
+  S* out = dst + (long long)nx * row + x0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    VecIO<S, V>::st(out, v[i]);
     out += p.plane;
   }
 }
@@ -121,7 +286,7 @@ __device__ __forceinline__ void post_stream(const S* f, const StepParams& p, con
   if (kind_h) {
     Nbr nb;
     make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
-    pull_cell<Q, S>(f, p, c.x, c.y, c.z, c.self, fl, nb, df);
+    pull_cell<Q, S>(f, p, c.x, c.y, c.z, fl & FLAG_TYPE, nb, df);
   } else {
 #pragma unroll
     for (int i = 0; i < Q; ++i) df[i] = Store<S>::ld(f + (long long)i * p.plane + c.self);
@@ -217,7 +382,11 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_reduce_partial(const S* f, const 
 // ---------------------------------------------------------------------------
 // Dispatch: one function per lattice, switching on storage and collision.
 
-template <int Q, typename S>
+// Launches the collision-dependent kernels for collision COLL and, for
+// COLL == COLL_BGK, also the collision-independent ones (init, readouts).
+// One translation unit instantiates this per (Q, storage, collision), so the
+// heavy KBC kernels compile in parallel with the rest.
+template <int Q, typename S, int COLL>
 int launch_typed(Op op, const LaunchArgs& a) {
   const StepParams& p = a.p;
   const long long rows = (long long)p.ny * p.nz;
@@ -229,40 +398,54 @@ int launch_typed(Op op, const LaunchArgs& a) {
   cudaStream_t st = (cudaStream_t)a.stream;
   switch (op) {
     case OP_STEP:
-      if (a.coll == COLL_NONE)
-        k_stream_collide<Q, S, COLL_NONE><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, p);
-      else if (a.coll == COLL_BGK)
-        k_stream_collide<Q, S, COLL_BGK><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, p);
-      else if (Q != 19)
-        k_stream_collide<Q, S, (Q == 19 ? COLL_BGK : COLL_KBC)><<<grid, block, 0, st>>>((const S*)a.src,
-                                                                                          (S*)a.dst, p);
-      else
-        return -2;
-      break;
+      k_stream_collide<Q, S, COLL><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, p);
+      return 0;
+    case OP_STEP_VEC: {
+      // 16-bit storage, BGK / NONE, D2Q9 / D3Q19 only (FP32 is faster with one
+      // cell per thread; on D3Q27 the 4 x 27 live values do not pay), V = 4
+      constexpr int V = 4;
+      if constexpr (sizeof(S) == 2 && Q != 27 && COLL != COLL_KBC) {
+        if (p.nx % V != 0) return -7;
+        const long long spr = (p.nx / V + 31) / 32 * 32;
+        const long long blocks = (spr * p.ny * p.nz + 127) / 128;
+        if (blocks > 0x7fffffffLL) return -1;
+        k_sc_vec<Q, S, COLL, V><<<(unsigned)blocks, 128, 0, st>>>((const S*)a.src, (S*)a.dst, p);
+        return 0;
+      }
+      return -7;
+    }
+    case OP_BOUNDARY: {
+      const long long tot = a.n_links + a.n_fix;
+      if (tot <= 0) return 0;
+      if (tot > 0x7fffffffLL) return -1;
+      const unsigned g = (unsigned)((tot + ROW_BLOCK - 1) / ROW_BLOCK);
+      k_boundary<Q, S, COLL><<<g, ROW_BLOCK, 0, st>>>((const S*)a.src, (S*)a.dst, p, a.links, (int)a.n_links, a.fix,
+                                                     (int)a.n_fix, a.recompute);
+      return 0;
+    }
     case OP_COLLIDE_LOCAL:
-      if (a.coll == COLL_NONE)
-        k_collide_local<Q, S, COLL_NONE><<<grid, block, 0, st>>>((S*)a.dst, p);
-      else if (a.coll == COLL_BGK)
-        k_collide_local<Q, S, COLL_BGK><<<grid, block, 0, st>>>((S*)a.dst, p);
-      else if (Q != 19)
-        k_collide_local<Q, S, (Q == 19 ? COLL_BGK : COLL_KBC)><<<grid, block, 0, st>>>((S*)a.dst, p);
-      else
-        return -2;
-      break;
-    case OP_INIT:
-      k_init<Q, S><<<grid, block, 0, st>>>((S*)a.dst, p, a.rho, a.u, a.ucs);
-      break;
-    case OP_MACRO:
-      k_macroscopic<Q, S><<<grid, block, 0, st>>>((const S*)a.src, p, a.kind_h, a.rho_out, a.u_out, a.ucs);
-      break;
-    case OP_REDUCE_PARTIAL:
-      if (a.partial_capacity < nblk) return -3;
-      k_reduce_partial<Q, S><<<grid, block, 0, st>>>((const S*)a.src, p, a.kind_h, a.partial);
-      break;
+      k_collide_local<Q, S, COLL><<<grid, block, 0, st>>>((S*)a.dst, p);
+      return 0;
     default:
-      return -4;
+      break;
   }
-  return 0;
+  if constexpr (COLL == COLL_BGK) {
+    switch (op) {
+      case OP_INIT:
+        k_init<Q, S><<<grid, block, 0, st>>>((S*)a.dst, p, a.rho, a.u, a.ucs);
+        return 0;
+      case OP_MACRO:
+        k_macroscopic<Q, S><<<grid, block, 0, st>>>((const S*)a.src, p, a.kind_h, a.rho_out, a.u_out, a.ucs);
+        return 0;
+      case OP_REDUCE_PARTIAL:
+        if (a.partial_capacity < nblk) return -3;
+        k_reduce_partial<Q, S><<<grid, block, 0, st>>>((const S*)a.src, p, a.kind_h, a.partial);
+        return 0;
+      default:
+        break;
+    }
+  }
+  return -4;
 }
 
 }  // namespace xlb

@@ -125,4 +125,94 @@ struct Store<__nv_bfloat16> {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Vector access to V consecutive stored populations (V * sizeof(S) = 8 or 16
+// bytes, naturally aligned), converted to / from FP32.
+
+template <typename S, int V>
+struct VecIO;
+
+template <>
+struct VecIO<float, 4> {
+  __device__ __forceinline__ static void ld(const float* p, float (&v)[4]) {
+    const float4 w = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+  }
+  __device__ __forceinline__ static void st(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+
+template <>
+struct VecIO<float, 2> {
+  __device__ __forceinline__ static void ld(const float* p, float (&v)[2]) {
+    const float2 w = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = w.x; v[1] = w.y;
+  }
+  __device__ __forceinline__ static void st(float* p, const float (&v)[2]) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  }
+};
+
+template <typename H>
+struct Half2Ops;
+template <>
+struct Half2Ops<__half> {
+  using T2 = __half2;
+  __device__ __forceinline__ static float2 to_f2(T2 h) { return __half22float2(h); }
+  __device__ __forceinline__ static T2 from_f2(float a, float b) { return __floats2half2_rn(a, b); }
+};
+template <>
+struct Half2Ops<__nv_bfloat16> {
+  using T2 = __nv_bfloat162;
+  __device__ __forceinline__ static float2 to_f2(T2 h) { return __bfloat1622float2(h); }
+  __device__ __forceinline__ static T2 from_f2(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+
+// 16-bit storage: V = 8 (one 16-byte word group) or V = 4 (8 bytes)
+template <typename H, int V>
+struct VecIO16 {
+  static constexpr int W = V / 2;  // 32-bit words
+  using O = Half2Ops<H>;
+  __device__ __forceinline__ static void ld(const H* p, float (&v)[V]) {
+    uint32_t w[W];
+    if (W == 4) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+      w[0] = q.x; w[1] = q.y; if (W == 4) { w[2 % W] = q.z; w[3 % W] = q.w; }
+    } else {
+      const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+      w[0] = q.x; w[1 % W] = q.y;
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      typename O::T2 h;
+      memcpy(&h, &w[k], 4);
+      const float2 f = O::to_f2(h);
+      v[2 * k] = f.x;
+      v[2 * k + 1] = f.y;
+    }
+  }
+  __device__ __forceinline__ static void st(H* p, const float (&v)[V]) {
+    uint32_t w[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      const typename O::T2 h = O::from_f2(v[2 * k], v[2 * k + 1]);
+      memcpy(&w[k], &h, 4);
+    }
+    if (W == 4)
+      *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1 % W], w[2 % W], w[3 % W]);
+    else
+      *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1 % W]);
+  }
+};
+
+template <>
+struct VecIO<__half, 8> : VecIO16<__half, 8> {};
+template <>
+struct VecIO<__half, 4> : VecIO16<__half, 4> {};
+template <>
+struct VecIO<__nv_bfloat16, 8> : VecIO16<__nv_bfloat16, 8> {};
+template <>
+struct VecIO<__nv_bfloat16, 4> : VecIO16<__nv_bfloat16, 4> {};
+
 }  // namespace xlb

@@ -2,6 +2,7 @@
 // kernel translation units.  Plain pointers and sizes only.
 #pragma once
 #include <stdint.h>
+#include <vector_types.h>
 
 #include "xlb_types.h"
 
@@ -12,7 +13,9 @@ enum Op {
   OP_COLLIDE_LOCAL = 1,  // in place on dst: dst = C(dst)
   OP_INIT = 2,           // dst = f^eq(rho, u) (and the boundary cells' values)
   OP_MACRO = 3,          // rho_out, u_out from src
-  OP_REDUCE_PARTIAL = 4  // block partial sums of mass and momentum
+  OP_REDUCE_PARTIAL = 4, // block partial sums of mass and momentum
+  OP_STEP_VEC = 7,       // fused stream + collide, V cells per thread, vector loads
+  OP_BOUNDARY = 8        // ghost values of the boundary links + inlet / outlet recompute
 };
 
 struct LaunchArgs {
@@ -29,6 +32,11 @@ struct LaunchArgs {
   float* u_out;
   double* partial;
   long long partial_capacity;  // rows of 4 doubles available in partial
+  const int2* links;           // OP_BOUNDARY ghost links {cell, dir | type << 8}
+  long long n_links;
+  const int* fix;              // OP_BOUNDARY inlet / outlet cells
+  long long n_fix;
+  int recompute;               // OP_BOUNDARY: recompute the inlet / outlet cells from src
   void* stream;
 };
 
@@ -46,5 +54,14 @@ long long row_blocks(const StepParams& p);
 int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int ny, int nz, int* err_word,
                         void* stream);
 int launch_reduce_final(const double* partial, long long n, double* out, void* stream);
+
+// Boundary tables of a mask: per block of 256 cells the number of links and
+// of inlet / outlet cells (counts[2b], counts[2b+1]); then, at the exclusive
+// offsets offs[2b], offs[2b+1], the links {cell, dir | type << 8} and the
+// inlet / outlet cells, in ascending cell order.
+long long bnd_list_blocks(long long n);
+int launch_bnd_count(int Q, const uint8_t* flags, int nx, int ny, int nz, int* counts, void* stream);
+int launch_bnd_write(int Q, const uint8_t* flags, int nx, int ny, int nz, const long long* offs, int2* links,
+                     int* fix, void* stream);
 
 }  // namespace xlb

@@ -55,27 +55,6 @@ __device__ __forceinline__ void pull_periodic(const S* __restrict__ src, long lo
   }
 }
 
-// Boundary rules applied on top of a periodic pull, for a source cell x - c_i
-// of type  fluid-like: keep h_i(x - c_i);   WALL: h_opp(i)(x);
-//   LID: h_opp(i)(x) + 2 w_i rho_w (c_i . u_w) / cs^2;   EQ: f_i^eq(rho_w, u_w).
-template <int Q, typename S>
-__device__ __forceinline__ void patch_masked(const S* __restrict__ src, const StepParams& p, const Nbr& nb,
-                                             int self, float (&df)[Q]) {
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const int t = __ldg(p.flags + src_index<Q>(nb, i)) & FLAG_TYPE;
-    if (!fluid_like(t)) {
-      if (t == EQ) {
-        df[i] = p.eq_df[i];
-      } else {
-        float v = Store<S>::ld(src + (long long)opposite<Q>(i) * p.plane + self);
-        if (t == LID) v += p.lid_term[i];
-        df[i] = v;
-      }
-    }
-  }
-}
-
 // Zou-He velocity inlet (inflow along +x; unknown populations have c_x = +1):
 //   rho = [sum_{c_x=0} f_i + 2 sum_{c_x=-1} f_i] / (1 - u_x),
 //   f_i = f_opp(i) + f_i^eq - f_opp(i)^eq = f_opp(i) + 6 w_i rho (c_i . u).
@@ -99,33 +78,26 @@ __device__ __forceinline__ void zou_he_inlet(const StepParams& p, float (&df)[Q]
   }
 }
 
-// The rules of a FLAG_SLOW cell on top of its periodic pull: mask
-// substitution, then Zou-He on INLET cells, then the zero-gradient outflow on
-// OUTLET cells (c_x = -1 populations taken from the pull at x - 1).
+// Post-stream populations of a fluid-like cell.  The stored state carries
+// ghost values in every WALL / LID / EQ cell (see k_boundary), so the
+// periodic pull already applies the bounce-back, moving-wall and equilibrium
+// rules; INLET cells then rebuild their c_x = +1 populations by Zou-He and
+// OUTLET cells copy their c_x = -1 populations from the pull at x - 1
+// (zero-gradient outflow).
 template <int Q, typename S>
-__device__ __forceinline__ void slow_rules(const S* __restrict__ src, const StepParams& p, int x, int y, int z,
-                                        int self, int type, const Nbr& nb, float (&df)[Q]) {
-  patch_masked<Q, S>(src, p, nb, self, df);
+__device__ __forceinline__ void pull_cell(const S* __restrict__ src, const StepParams& p, int x, int y, int z,
+                                          int type, const Nbr& nb, float (&df)[Q]) {
+  pull_periodic<Q, S>(src, p.plane, nb, df);
   if (type == INLET) zou_he_inlet<Q>(p, df);
   if (type == OUTLET) {
-    const int xl = wrap_m(x, p.nx);
     Nbr nl;
-    make_nbr(nl, xl, y, z, p.nx, p.ny, p.nz);
+    make_nbr(nl, wrap_m(x, p.nx), y, z, p.nx, p.ny, p.nz);
     float dl[Q];
     pull_periodic<Q, S>(src, p.plane, nl, dl);
-    patch_masked<Q, S>(src, p, nl, self - x + xl, dl);
 #pragma unroll
     for (int i = 0; i < Q; ++i)
       if (Lattice<Q>::c(i, 0) == -1) df[i] = dl[i];
   }
-}
-
-// Full post-stream populations of a fluid-like cell with every boundary rule.
-template <int Q, typename S>
-__device__ __forceinline__ void pull_cell(const S* __restrict__ src, const StepParams& p, int x, int y, int z,
-                                          int self, int fl, const Nbr& nb, float (&df)[Q]) {
-  pull_periodic<Q, S>(src, p.plane, nb, df);
-  if (fl & FLAG_SLOW) slow_rules<Q, S>(src, p, x, y, z, self, fl & FLAG_TYPE, nb, df);
 }
 
 template <int Q>

@@ -36,7 +36,11 @@ struct StepParams {
   float eq_df[27];       // f_i^eq(rho_eq, u_eq) - w_i (equilibrium-BC cells)
   float eq_rho, eq_u[3];
   float inlet_u[3];      // Zou-He inlet velocity
+  int* err;              // device error word for kernels with bounded waits
 };
+
+// Device error codes written to StepParams::err.
+constexpr int DEVERR_TIMEOUT = 1;
 
 // Deviation storage: populations are stored as f_i - w_i * RHO0.
 constexpr float RHO0 = 1.0f;

@@ -24,6 +24,7 @@ XLB_OK, XLB_ERR_ARG, XLB_ERR_UNSUPPORTED, XLB_ERR_OOM, XLB_ERR_CUDA, XLB_ERR_TIM
 XLB_D2Q9, XLB_D3Q19, XLB_D3Q27 = 9, 19, 27
 XLB_COLL_NONE, XLB_COLL_BGK, XLB_COLL_KBC = 0, 1, 2
 XLB_STORE_F32, XLB_STORE_F16, XLB_STORE_BF16 = 0, 1, 2
+XLB_KERNEL_AUTO, XLB_KERNEL_DIRECT, XLB_KERNEL_VEC = 0, 1, 2
 XLB_CELL_FLUID, XLB_CELL_WALL, XLB_CELL_LID, XLB_CELL_INLET, XLB_CELL_OUTLET, XLB_CELL_EQ = range(6)
 
 STORAGE = {"f32": XLB_STORE_F32, "f16": XLB_STORE_F16, "bf16": XLB_STORE_BF16}
@@ -47,6 +48,7 @@ _PROTOS = {
     "xlb_omega_from_nu": (_d, [_d]),
     "xlb_set_mask": (_i, [_vp, _vp]),
     "xlb_set_bc": (_i, [_vp, _i, _f, C.POINTER(_f)]),
+    "xlb_boundary_links": (_i, [_vp, C.POINTER(_i64), C.POINTER(_i64)]),
     "xlb_set_force": (_i, [_vp, C.POINTER(_f)]),
     "xlb_init": (_i, [_vp, _vp, _vp]),
     "xlb_step": (_i, [_vp, _i64]),
@@ -63,6 +65,8 @@ _PROTOS = {
     "xlb_adjoint_step": (_i, [_vp, _i64]),
     "xlb_adjoint_init_grad": (_i, [_vp, _vp, _vp]),
     "xlb_tape_end": (_i, [_vp]),
+    "xlb_set_kernel": (_i, [_vp, _i]),
+    "xlb_get_kernel": (_i, [_vp, C.POINTER(_i)]),
     "xlb_profile_enable": (_i, [_vp, _i]),
     "xlb_profile_read": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_i64)]),
 }
@@ -153,6 +157,12 @@ def xlb_set_mask(ctx, mask):
     _check(load().xlb_set_mask(ctx, _ptr(mask)), ctx)
 
 
+def xlb_boundary_links(ctx):
+    nl, nf = C.c_int64(), C.c_int64()
+    _check(load().xlb_boundary_links(ctx, C.byref(nl), C.byref(nf)), ctx)
+    return nl.value, nf.value
+
+
 def xlb_set_bc(ctx, cell_type, rho, u):
     _check(load().xlb_set_bc(ctx, int(cell_type), float(rho), _vec3(u)), ctx)
 
@@ -236,6 +246,16 @@ def xlb_tape_end(ctx):
     _check(load().xlb_tape_end(ctx), ctx)
 
 
+def xlb_set_kernel(ctx, variant=XLB_KERNEL_AUTO):
+    _check(load().xlb_set_kernel(ctx, int(variant)), ctx)
+
+
+def xlb_get_kernel(ctx):
+    v = C.c_int()
+    _check(load().xlb_get_kernel(ctx, C.byref(v)), ctx)
+    return v.value
+
+
 def xlb_profile_enable(ctx, on=True):
     _check(load().xlb_profile_enable(ctx, int(bool(on))), ctx)
 
@@ -282,6 +302,13 @@ class Simulation:
 
     def set_force(self, F):
         xlb_set_force(self.ctx, F)
+
+    def set_kernel(self, variant="auto"):
+        v = {"auto": XLB_KERNEL_AUTO, "direct": XLB_KERNEL_DIRECT, "vec": XLB_KERNEL_VEC}.get(variant, variant)
+        xlb_set_kernel(self.ctx, v)
+
+    def kernel(self):
+        return xlb_get_kernel(self.ctx)
 
     def init(self, rho=None, u=None):
         xlb_init(self.ctx, rho, u)

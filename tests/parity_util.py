@@ -55,8 +55,9 @@ class Case:
         f = O.run(self.lat, f, self.mask, p, steps)
         return O.macroscopic(self.lat, f, self.mask, p), f
 
-    def gpu_sim(self, storage="f32"):
+    def gpu_sim(self, storage="f32", variant="auto"):
         sim = X.Simulation(self.q, self.dims, self.omega, self.collision, storage)
+        sim.set_kernel(variant)
         if self.mask.any():
             sim.set_mask(np.ascontiguousarray(self.mask, dtype=np.uint8))
         if self.lid:
@@ -71,8 +72,8 @@ class Case:
                  np.ascontiguousarray(self.u0, dtype=np.float32))
         return sim
 
-    def gpu(self, steps, storage="f32"):
-        sim = self.gpu_sim(storage)
+    def gpu(self, steps, storage="f32", variant="auto"):
+        sim = self.gpu_sim(storage, variant)
         sim.step(steps)
         rho, u = sim.macroscopic()
         sim.close()

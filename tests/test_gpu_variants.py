@@ -1,0 +1,124 @@
+"""Bulk-pass variants and the boundary tables.
+
+The two bulk variants (one cell per thread, and four cells per thread with
+vector loads and warp shuffles) give identical populations; the boundary
+tables (ghost links and inlet / outlet cells) have the sizes the mask fixes;
+ghost values follow changes of the lid velocity and of the mask mid-run.
+"""
+import numpy as np
+import pytest
+
+from oracle import lbm as O
+from paper_2311_16080_gb300 import inputs as I
+from paper_2311_16080_gb300 import xlb as X
+from parity_util import Case, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    out = []
+    m = I.lid_driven_cavity_mask(32, 24, 20)
+    out.append(("cavity19", Case(19, m.shape, 1.7, "bgk", mask=m, lid=(1.0, (0.05, 0.0, 0.0)))))
+    sh = (40, 64)
+    m = I.channel_2d_mask(64, 40, top=O.LID)
+    m[I.random_obstacle_mask(sh, 0.06, seed=3) > 0] = O.WALL
+    m[I.random_obstacle_mask(sh, 0.02, seed=4) > 0] = O.EQ
+    r, u = I.random_flow(sh, 2, seed=5, rho_amp=0.005, u_amp=0.02)
+    out.append(("mixed9", Case(9, sh, 1.3, "bgk", mask=m, force=(1e-5, 2e-6, 0.0),
+                               lid=(1.0, (0.03, 0.0, 0.0)), eq=(1.0, (0.01, 0.0, 0.0)), rho0=r, u0=u)))
+    r, u = I.random_flow((8, 12, 48), 3, seed=6, rho_amp=0.01, u_amp=0.03)
+    out.append(("periodic27", Case(27, (8, 12, 48), 1.5, "bgk", rho0=r, u0=u)))
+    m = I.lid_driven_cavity_mask(72, 10, 12)  # 72 / 4 = 18 slots: partial warps
+    out.append(("ragged19", Case(19, m.shape, 1.7, "bgk", mask=m, lid=(1.0, (0.05, 0.0, 0.0)))))
+    return out
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_vec_equals_direct(name, case, storage):
+    if case.q == 27:
+        pytest.skip("the vectorised kernel covers D2Q9 / D3Q19")
+    a = case.gpu_sim(storage, "direct")
+    b = case.gpu_sim(storage, "vec")
+    assert a.kernel() == X.XLB_KERNEL_DIRECT and b.kernel() == X.XLB_KERNEL_VEC
+    a.step(40)
+    b.step(40)
+    pa, _ = a.populations()
+    pb, _ = b.populations()
+    fl = O.fluid_like(case.mask)
+    assert np.array_equal(pa[:, fl], pb[:, fl])
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
+def test_vec_f16_matches_oracle(name, case):
+    if case.q == 27:
+        pytest.skip("the vectorised kernel covers D2Q9 / D3Q19")
+    (rho_o, u_o), _ = case.oracle(120)
+    rho_g, u_g = case.gpu(120, "f16", "vec")
+    fl = O.fluid_like(case.mask)
+    assert rel_l2(u_g[:, fl], u_o[:, fl]) <= 5e-3
+
+
+def test_auto_picks_vec_for_16_bit_storage_only():
+    m = I.lid_driven_cavity_mask(32, 8, 8)
+    c = Case(19, m.shape, 1.5, "bgk", mask=m)
+    s32 = c.gpu_sim("f32")
+    s16 = c.gpu_sim("f16")
+    assert s32.kernel() == X.XLB_KERNEL_DIRECT
+    assert s16.kernel() == X.XLB_KERNEL_VEC
+    with pytest.raises(X.XlbError) as e:
+        X.xlb_set_kernel(s32.ctx, X.XLB_KERNEL_VEC)
+    assert e.value.status == X.XLB_ERR_UNSUPPORTED
+    odd = Case(9, (30, 45), 1.2).gpu_sim("f16")
+    assert odd.kernel() == X.XLB_KERNEL_DIRECT  # nx % 4 != 0
+    for s in (s32, s16, odd):
+        s.close()
+
+
+def test_boundary_tables():
+    """One ghost link per (fluid cell, direction) whose source is WALL, LID or
+    EQ, and one fix-up entry per inlet / outlet cell."""
+    for q, m in ((19, I.lid_driven_cavity_mask(20, 18, 16)),
+                 (27, I.sphere_channel_mask(40, 16, 12, radius=3, center=(12, 8, 6))),
+                 (9, np.where(I.random_obstacle_mask((30, 40), 0.1, seed=2) > 0, O.EQ, 0).astype(np.uint8))):
+        lat = O.Lattice(q)
+        links = 0
+        for i in range(1, q):
+            links += int(((m == O.FLUID) & ~O.fluid_like(lat.roll(m, i))).sum())
+        fix = int(np.isin(m, (O.INLET, O.OUTLET)).sum())
+        s = X.Simulation(q, tuple(reversed(m.shape)), 1.5, "bgk")
+        s.set_mask(m)
+        assert X.xlb_boundary_links(s.ctx) == (links, fix)
+        s.close()
+
+
+def test_ghosts_follow_lid_and_mask_changes():
+    """Changing the lid velocity or the mask between steps takes effect at
+    the next step exactly as in the oracle (the ghost values are refreshed)."""
+    m1 = I.channel_2d_mask(48, 20, top=O.LID)
+    m2 = m1.copy()
+    m2[8:12, 20:24] = O.WALL
+    c = Case(9, m1.shape, 1.4, "bgk", mask=m1, lid=(1.0, (0.04, 0.0, 0.0)))
+    sim = c.gpu_sim()
+    sim.step(30)
+    sim.set_bc(X.XLB_CELL_LID, 1.0, (-0.02, 0.01, 0.0))
+    sim.step(30)
+    sim.set_mask(m2)
+    sim.step(30)
+    _, ug = sim.macroscopic()
+    sim.close()
+    lat = c.lat
+    p = c.params()
+    f = O.run(lat, O.init_state(lat, c.rho0, c.u0, m1, p), m1, p, 30)
+    p.bc.lid_u = [-0.02, 0.01]
+    f = O.run(lat, f, m1, p, 30)
+    f = O.run(lat, f, m2, p, 30)
+    _, uo = O.macroscopic(lat, f, m2, p)
+    fl = O.fluid_like(m2)
+    assert rel_l2(ug[:, fl], uo[:, fl]) <= 1e-4
