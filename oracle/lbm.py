@@ -43,7 +43,8 @@ Readings of points the paper leaves open (each also listed in the design doc):
 * INLET cells apply Zou-He velocity reconstruction for the populations with
   c_x = +1 (non-equilibrium bounce-back of every unknown, no transverse term);
 * OUTLET cells copy their c_x = -1 populations from the cell at x-1
-  (zero-gradient extrapolation);
+  (zero-gradient extrapolation) -- parity unpinned: nothing but its own
+  definition checks this rule;
 * observables are those of the post-stream state f_t; the reported velocity
   with a body force is (j + F/2) / rho;
 * solid (WALL, LID) cells report rho = 0, u = 0.
@@ -321,7 +322,9 @@ def zou_he_inlet(lat: Lattice, f, mask, bc: BC):
 
 def outflow(lat: Lattice, f_plain, f, mask):
     """Zero-gradient outflow on OUTLET cells: populations with c_x = -1 take
-    the value that the pull rule gives at the cell x - 1."""
+    the value that the pull rule gives at the cell x - 1.  Parity unpinned:
+    the paper only cites an extrapolation scheme, so no closed form or
+    printed value checks this reading."""
     sel = mask == OUTLET
     if not sel.any():
         return f
