@@ -154,6 +154,27 @@ int xlb_reduce(xlb_ctx* ctx, double out_mass[1], double out_mom[3]);
  * steps are invalid). */
 int xlb_synchronize(xlb_ctx* ctx);
 
+/* FP64 totals of stored populations without any device allocation.  The
+ * paper has no counterpart: this serves callers that must not call
+ * cudaMalloc (code capturing or replaying a CUDA graph, real-time loops that
+ * pre-allocate everything, hosts that own all device memory through their
+ * own pools).  It reduces `populations` (device memory: Q planes of
+ * plane_stride elements of the storage type, each holding f_i - w_i for the
+ * N = nx*ny*nz cells, x fastest -- the layout xlb_populations exposes) over
+ * the fluid-like cells of `mask` (device memory, uint8 XLB_CELL_* codes; NULL
+ * = all cells): out[0] = sum rho, out[1..3] = sum j.  `out` is 4 doubles in
+ * device memory (written on the stream) or host memory (the call then
+ * synchronises the stream).  The partial sums live in one fixed array of
+ * 128 KiB compiled into the library, which every GPU that loads it keeps
+ * until the process exits: at most 67,108,864 cells (4096 partial sums of
+ * 16384 cells); larger lattices give XLB_ERR_ARG.  The first call on a device
+ * looks up the array's address with that device current; make that first call
+ * before capturing any stream.  Calls share the array: calls that overlap on
+ * the GPU race, so order them on one stream.  Each call rewrites every
+ * partial it reads, so nothing needs clearing between calls. */
+int xlb_moments_noalloc(int lattice, const int64_t dims[3], int storage, const void* populations,
+                        int64_t plane_stride, const uint8_t* mask, double* out, void* cuda_stream);
+
 /* ---- checkpoint / resume (Section 3.7) --------------------------------- */
 
 /* Size in bytes of a serialized state (header + populations). */

@@ -56,6 +56,7 @@ _PROTOS = {
     "xlb_macroscopic": (_i, [_vp, _vp, _vp]),
     "xlb_reduce": (_i, [_vp, C.POINTER(_d), C.POINTER(_d)]),
     "xlb_synchronize": (_i, [_vp]),
+    "xlb_moments_noalloc": (_i, [_i, C.POINTER(_i64), _i, _vp, _i64, _vp, _vp, _vp]),
     "xlb_state_bytes": (_i, [_vp, C.POINTER(C.c_size_t)]),
     "xlb_state_get": (_i, [_vp, _vp, C.c_size_t]),
     "xlb_state_set": (_i, [_vp, _vp, C.c_size_t]),
@@ -198,6 +199,18 @@ def xlb_reduce(ctx):
 
 def xlb_synchronize(ctx):
     _check(load().xlb_synchronize(ctx), ctx)
+
+
+def xlb_moments_noalloc(lattice, dims, storage, populations, plane_stride, mask, out, cuda_stream=None):
+    """FP64 (mass, j_x, j_y, j_z) of stored populations, allocating nothing
+    (the library's fixed scratch array); ``out`` holds 4 doubles (host or
+    device)."""
+    d = list(dims) + [1] * (3 - len(dims))
+    arr = (C.c_int64 * 3)(*[int(x) for x in d])
+    s = load().xlb_moments_noalloc(int(lattice), arr, int(storage), _ptr(populations), int(plane_stride),
+                                   _ptr(mask), _ptr(out), cuda_stream)
+    if s != XLB_OK:
+        raise XlbError(s, "xlb_moments_noalloc rejected its arguments or a CUDA call failed")
 
 
 def xlb_state_bytes(ctx):
