@@ -132,7 +132,7 @@ def run_ours(args, rank, world, dist):
     assert stream.cuda_stream != 0
     n = args.size
     cells = n ** 3
-    sim, mask = _cavity_sim(torch, X, I, n, "f32", stream.cuda_stream)
+    sim, mask = _cavity_sim(torch, X, I, n, args.storage, stream.cuda_stream)
     if args.kernel != "auto":
         sim.set_kernel(args.kernel)
     kname = ("k_sc_vec<19,float,BGK,4> (4 cells per thread)" if sim.kernel() == X.XLB_KERNEL_VEC
@@ -191,7 +191,8 @@ def run_ours(args, rank, world, dist):
            "d2h_bytes_per_step": 4 * (o_rho.numel() + o_u.numel()) / args.steps}
 
     peak, peak_kind = hbm_peak()
-    algo_bytes = BYTES_PER_CELL_F32 * fluid + cells  # populations of fluid cells + the mask byte
+    esz = 4 if args.storage == "f32" else 2
+    algo_bytes = 2 * 19 * esz * fluid + cells  # populations of fluid cells + the mask byte
     achieved = algo_bytes / (ms_step * 1e-3) / 1e9
     if achieved > 1.15 * peak:
         raise RuntimeError(f"timed kernel exceeds the measured copy bandwidth ({achieved:.0f} GB/s): "
@@ -406,6 +407,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--kernel", choices=["auto", "direct", "vec"], default="auto")
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
+                    help="population storage (default f32, the benchmark workload; others for profiling)")
     ap.add_argument("--size", type=int, default=N_CAV,
                     help="cavity edge (default 256, the benchmark workload; smaller only for profiling)")
     args = ap.parse_args()

@@ -225,7 +225,9 @@ int xlb_tape_end(xlb_ctx* ctx);
  *   XLB_KERNEL_VEC:    4 consecutive cells per thread, one aligned 4-wide load
  *     per direction, the +-x neighbour element exchanged by warp shuffles
  *     (16-bit storage, D2Q9 / D3Q19, BGK / NONE, nx % 4 == 0);
- *   XLB_KERNEL_AUTO:   VEC where possible, else DIRECT (the default). */
+ *   XLB_KERNEL_AUTO:   VEC where possible on lattices without boundary faces
+ *     (whole face planes the mask fills with one boundary type), else DIRECT
+ *     (the default). */
 enum { XLB_KERNEL_AUTO = 0, XLB_KERNEL_DIRECT = 1, XLB_KERNEL_VEC = 2 };
 
 /* Choose the variant (XLB_ERR_UNSUPPORTED if it cannot run this ctx). */

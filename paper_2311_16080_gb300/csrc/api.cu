@@ -46,6 +46,7 @@ struct xlb_ctx {
   long long n_links = 0;
   int* fix = nullptr;  // inlet / outlet cells (recomputed after a bulk pass)
   long long n_fix = 0;
+  int face[6] = {0, 0, 0, 0, 0, 0};  // described boundary faces (StepParams::face)
   bool has_inlet_outlet = false;
   float* init_fields = nullptr;  // (1 + D) * N: rho0, u0 (component-major)
   bool has_init = false;
@@ -154,6 +155,11 @@ static StepParams make_params(const xlb_ctx* c) {
   }
   p.eq_rho = c->eq_rho;
   p.err = c->err_word ? c->err_word + 1 : nullptr;
+  p.has_faces = 0;
+  for (int f = 0; f < 6; ++f) {
+    p.face[f] = c->face[f];
+    p.has_faces |= c->face[f] != 0;
+  }
   // constant boundary terms per direction, in double then rounded once
   auto fill = [&](auto lat_tag) {
     constexpr int Q = decltype(lat_tag)::value;
@@ -226,9 +232,15 @@ static bool vec_possible(const xlb_ctx* c) {
   return c->esize == 2 && c->Q != 27 && c->coll != XLB_COLL_KBC && c->nx % 4 == 0;
 }
 
+// AUTO takes VEC only on lattices without boundary faces: with faces, every
+// warp of a 4-cell-per-thread row holds a face-adjacent lane (measured slower
+// than one cell per thread on the 256^3 cavity).
 static bool use_vec(const xlb_ctx* c) {
-  if (c->variant == XLB_KERNEL_DIRECT) return false;
-  return vec_possible(c);
+  if (c->variant == XLB_KERNEL_DIRECT || !vec_possible(c)) return false;
+  if (c->variant == XLB_KERNEL_VEC) return true;
+  for (int f = 0; f < 6; ++f)
+    if (c->face[f]) return false;
+  return true;
 }
 
 // Boundary pass on dst after a pass that produced post-collision values
@@ -307,6 +319,84 @@ static int launch_init(xlb_ctx* c, void* dst) {
   a.rho = c->init_fields;
   a.u = c->init_fields + c->N;
   return dispatch(c, OP_INIT, a);
+}
+
+// Boundary faces of a mask (host copy): a face plane qualifies when none of
+// its cells is fluid-like; its type is that of the plane's centre cell.  A
+// face stays only while every cell of its plane has the type the pull derives
+// from the remaining faces (WALL wins where planes meet; at most one other
+// type among LID / EQ); dropped faces are covered by ghost links.
+static void detect_faces(const uint8_t* m, long long nx, long long ny, long long nz, int out[6]) {
+  for (int f = 0; f < 6; ++f) out[f] = 0;
+  const long long ext[3] = {nx, ny, nz};
+  auto at = [&](long long x, long long y, long long z) { return (int)m[x + nx * (y + ny * z)]; };
+  auto fl = [](int t) { return t == XLB_CELL_FLUID || t == XLB_CELL_INLET || t == XLB_CELL_OUTLET; };
+  int cand[6] = {0, 0, 0, 0, 0, 0};
+  for (int f = 0; f < 6; ++f) {
+    const int ax = f / 2;
+    if (ax == 2 && nz == 1) continue;
+    const long long pos = (f % 2) ? ext[ax] - 1 : 0;
+    const long long n1 = ext[(ax + 1) % 3], n2 = ext[(ax + 2) % 3];
+    bool ok = true;
+    for (long long a = 0; a < n1 && ok; ++a)
+      for (long long b = 0; b < n2 && ok; ++b) {
+        long long q[3];
+        q[ax] = pos;
+        q[(ax + 1) % 3] = a;
+        q[(ax + 2) % 3] = b;
+        ok = !fl(at(q[0], q[1], q[2]));
+      }
+    if (!ok) continue;
+    long long q[3];
+    q[ax] = pos;
+    q[(ax + 1) % 3] = n1 / 2;
+    q[(ax + 2) % 3] = n2 / 2;
+    const int t = at(q[0], q[1], q[2]);
+    if (t == XLB_CELL_WALL || t == XLB_CELL_LID || t == XLB_CELL_EQ) cand[f] = t;
+  }
+  int other = 0;
+  for (int f = 0; f < 6; ++f)
+    if (cand[f] && cand[f] != XLB_CELL_WALL) {
+      if (other && other != cand[f]) return;
+      other = cand[f];
+    }
+  // verify every cell of every qualifying plane; drop a face whose plane has
+  // a cell of another type than the faces derive, and check again
+  for (bool changed = true; changed;) {
+    changed = false;
+    for (int f = 0; f < 6 && !changed; ++f) {
+      if (!cand[f]) continue;
+      const int ax = f / 2;
+      const long long pos = (f % 2) ? ext[ax] - 1 : 0;
+      const long long n1 = ext[(ax + 1) % 3], n2 = ext[(ax + 2) % 3];
+      bool bad = false;
+      for (long long a = 0; a < n1 && !bad; ++a)
+        for (long long b = 0; b < n2 && !bad; ++b) {
+          long long q[3];
+          q[ax] = pos;
+          q[(ax + 1) % 3] = a;
+          q[(ax + 2) % 3] = b;
+          int tw = 0, to = 0;
+          for (int g = 0; g < 6; ++g) {
+            if (!cand[g]) continue;
+            const int gx = g / 2;
+            const long long gp = (g % 2) ? ext[gx] - 1 : 0;
+            if (q[gx] == gp) {
+              if (cand[g] == XLB_CELL_WALL)
+                tw = XLB_CELL_WALL;
+              else
+                to = cand[g];
+            }
+          }
+          bad = at(q[0], q[1], q[2]) != (tw ? tw : to);
+        }
+      if (bad) {
+        cand[f] = 0;
+        changed = true;
+      }
+    }
+  }
+  for (int f = 0; f < 6; ++f) out[f] = cand[f];
 }
 
 extern "C" {
@@ -433,6 +523,8 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
     dmask = (uint8_t*)mask;
   }
   uint8_t* nf = nullptr;
+  bool new_io = false;
+  int new_face[6] = {0, 0, 0, 0, 0, 0};
   CK(cudaMalloc(&nf, n));
   CK(cudaMemsetAsync(c->err_word, 0, sizeof(int), c->stream));
   if (launch_mask_prepare(c->Q, dmask, nf, (int)c->nx, (int)c->ny, (int)c->nz, c->err_word, c->stream) != 0) {
@@ -457,9 +549,10 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
     }
     bool io = false;
     for (size_t k = 0; k < n && !io; ++k) io = (hp[k] == XLB_CELL_INLET || hp[k] == XLB_CELL_OUTLET);
-    c->has_inlet_outlet = io;
+    new_io = io;
+    detect_faces(hp, c->nx, c->ny, c->nz, new_face);
   }
-  // boundary tables: ghost links and inlet / outlet cells
+  // boundary tables: ghost links (direction-major) and inlet / outlet cells
   int2* nlinks = nullptr;
   int* nfix = nullptr;
   long long nl = 0, nfx = 0;
@@ -467,29 +560,40 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
     const long long nb = bnd_list_blocks(c->N);
     int* counts = nullptr;
     long long* offs = nullptr;
-    cudaError_t e = cudaMalloc(&counts, sizeof(int) * 2 * nb);
-    if (e == cudaSuccess) e = cudaMalloc(&offs, sizeof(long long) * 2 * nb);
-    std::vector<int> hc(2 * nb);
-    std::vector<long long> ho(2 * nb);
-    if (e == cudaSuccess && launch_bnd_count(c->Q, nf, (int)c->nx, (int)c->ny, (int)c->nz, counts, c->stream) != 0)
-      e = cudaErrorInvalidValue;
+    cudaError_t e = cudaMalloc(&counts, sizeof(int) * nb * (c->Q + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&offs, sizeof(long long) * nb * (c->Q + 1));
+    std::vector<int> hc(nb * (c->Q + 1));
+    std::vector<long long> ho(nb * (c->Q + 1));
+    // passes 1..Q-1: links of direction i; pass Q: inlet / outlet cells
+    for (int pass = 1; pass <= c->Q && e == cudaSuccess; ++pass) {
+      const int mode = pass == c->Q ? 1 : 0;
+      if (launch_pred_count(mode, pass, c->Q, new_face, nf, (int)c->nx, (int)c->ny, (int)c->nz, counts + nb * pass,
+                            c->stream) != 0)
+        e = cudaErrorInvalidValue;
+    }
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(hc.data(), counts, sizeof(int) * 2 * nb, cudaMemcpyDeviceToHost, c->stream);
+      e = cudaMemcpyAsync(hc.data() + nb, counts + nb, sizeof(int) * nb * c->Q, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) {
-      for (long long b = 0; b < nb; ++b) {
-        ho[2 * b] = nl;
-        ho[2 * b + 1] = nfx;
-        nl += hc[2 * b];
-        nfx += hc[2 * b + 1];
+      for (int pass = 1; pass <= c->Q; ++pass) {
+        long long& run = pass == c->Q ? nfx : nl;
+        for (long long b = 0; b < nb; ++b) {
+          ho[nb * pass + b] = run;
+          run += hc[nb * pass + b];
+        }
       }
-      e = cudaMemcpyAsync(offs, ho.data(), sizeof(long long) * 2 * nb, cudaMemcpyHostToDevice, c->stream);
+      e = cudaMemcpyAsync(offs + nb, ho.data() + nb, sizeof(long long) * nb * c->Q, cudaMemcpyHostToDevice,
+                          c->stream);
     }
     if (e == cudaSuccess && nl > 0) e = cudaMalloc(&nlinks, sizeof(int2) * nl);
     if (e == cudaSuccess && nfx > 0) e = cudaMalloc(&nfix, sizeof(int) * nfx);
-    if (e == cudaSuccess && (nl > 0 || nfx > 0) &&
-        launch_bnd_write(c->Q, nf, (int)c->nx, (int)c->ny, (int)c->nz, offs, nlinks, nfix, c->stream) != 0)
-      e = cudaErrorInvalidValue;
+    for (int pass = 1; pass <= c->Q && e == cudaSuccess; ++pass) {
+      const int mode = pass == c->Q ? 1 : 0;
+      if ((mode == 0 && nl == 0) || (mode == 1 && nfx == 0)) continue;
+      if (launch_pred_write(mode, pass, c->Q, new_face, nf, (int)c->nx, (int)c->ny, (int)c->nz, offs + nb * pass,
+                            nlinks, nfix, c->stream) != 0)
+        e = cudaErrorInvalidValue;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (counts) cudaFree(counts);
     if (offs) cudaFree(offs);
@@ -517,6 +621,8 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
   c->n_links = nl;
   c->fix = nfix;
   c->n_fix = nfx;
+  c->has_inlet_outlet = new_io;
+  for (int f = 0; f < 6; ++f) c->face[f] = new_face[f];
   c->has_mask = true;
   return XLB_OK;
 }

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, COLL>::value)
   Nbr nb;
   make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
   float df[Q];
-  pull_periodic<Q, S>(src, p.plane, nb, df);
+  pull_periodic<Q, S>(src, p, nb, c.self, c.x, c.y, c.z, df);
   collide<Q, COLL>(df, p);
   S* out = dst + c.self;
 #pragma unroll
@@ -90,31 +90,52 @@ __device__ __forceinline__ void write_ghost(S* __restrict__ dst, const StepParam
 }
 
 // Boundary pass on dst, after a pass that wrote post-collision values there.
-// Threads [0, n_links) write the ghost values of the links of FLUID cells
-// (the link list).  Threads [n_links, n_links + n_fix) handle one INLET or
+// Threads [0, ceil(n_links / 4)) write the ghost values of the links of FLUID
+// cells (4 links each); the next n_fix threads handle one INLET or
 // OUTLET cell each: with `recompute`, its update from src with the full
 // rules (the bulk pass pulled it as if periodic); then the ghosts of its own
 // links.  src is read only by the recomputation, which needs the ghosts of
 // the previous state, already in src.
+constexpr int LINKS_PER_THREAD = 4;
+
 template <int Q, typename S, int COLL>
 __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ src, S* __restrict__ dst,
                                                         const StepParams p, const int2* __restrict__ links,
                                                         int n_links, const int* __restrict__ fix, int n_fix,
                                                         int recompute) {
+  // link threads: LINKS_PER_THREAD links each, strided by the link-thread
+  // count so that a warp's loads and stores stay on consecutive entries
+  const int n_lt = (n_links + LINKS_PER_THREAD - 1) / LINKS_PER_THREAD;
   const int k = blockIdx.x * ROW_BLOCK + threadIdx.x;
-  if (k < n_links) {
-    const int2 l = __ldg(links + k);
-    const int x = l.x, i = l.y & 0xff, t = l.y >> 8;
-    const int cx = x % p.nx, r = x / p.nx;
-    int io = 0;
+  if (k < n_lt) {
+    int2 l[LINKS_PER_THREAD];
+    float h[LINKS_PER_THREAD];
 #pragma unroll
-    for (int j = 1; j < Q; ++j)
-      if (j == i) io = opposite<Q>(j);
-    const float h = t == EQ ? 0.f : Store<S>::ld_plain(dst + (long long)io * p.plane + x);
-    write_ghost<Q, S>(dst, p, cx, r % p.ny, r / p.ny, i, t, h);
+    for (int m = 0; m < LINKS_PER_THREAD; ++m) {
+      const int e = k + m * n_lt;
+      l[m] = e < n_links ? __ldg(links + e) : make_int2(-1, 0);
+    }
+#pragma unroll
+    for (int m = 0; m < LINKS_PER_THREAD; ++m) {
+      h[m] = 0.f;
+      if (l[m].x >= 0 && (l[m].y >> 8) != EQ) {
+        int io = 0;
+        const int i = l[m].y & 0xff;
+#pragma unroll
+        for (int j = 1; j < Q; ++j)
+          if (j == i) io = opposite<Q>(j);
+        h[m] = Store<S>::ld_plain(dst + (long long)io * p.plane + l[m].x);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < LINKS_PER_THREAD; ++m) {
+      if (l[m].x < 0) continue;
+      const int x = l[m].x, r = x / p.nx;
+      write_ghost<Q, S>(dst, p, x - r * p.nx, r % p.ny, r / p.ny, l[m].y & 0xff, l[m].y >> 8, h[m]);
+    }
     return;
   }
-  const int kf = k - n_links;
+  const int kf = k - n_lt;
   if (kf >= n_fix) return;
   const int self = __ldg(fix + kf);
   const int x = self % p.nx;
@@ -188,6 +209,31 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
 #pragma unroll
       for (int c = 0; c < 3; ++c) rb[b][c] = nx * (ys[b] + ny * zs[c]);
   }
+  // face types of the source coordinates (x0 + k -+ 1, y -+ 1, z -+ 1)
+  int tx[V][3], ty[3] = {0, 0, 0}, tz[3] = {0, 0, 0};
+  bool near = false;
+#pragma unroll
+  for (int k = 0; k < V; ++k) tx[k][0] = tx[k][1] = tx[k][2] = 0;
+  if (p.has_faces) {
+    const int fy0 = face_code(wrap_m(y, ny), ny), fy2 = face_code(wrap_p(y, ny), ny);
+    ty[0] = (fy0 & 1 ? p.face[2] : 0) | (fy0 & 2 ? p.face[3] : 0);
+    ty[2] = (fy2 & 1 ? p.face[2] : 0) | (fy2 & 2 ? p.face[3] : 0);
+    if (nz > 1) {
+      const int fz0 = face_code(wrap_m(z, nz), nz), fz2 = face_code(wrap_p(z, nz), nz);
+      tz[0] = (fz0 & 1 ? p.face[4] : 0) | (fz0 & 2 ? p.face[5] : 0);
+      tz[2] = (fz2 & 1 ? p.face[4] : 0) | (fz2 & 2 ? p.face[5] : 0);
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const int x = x0 + k;
+      const int fxm = face_code(x == 0 ? nx - 1 : x - 1, nx), fxp = face_code(x == nx - 1 ? 0 : x + 1, nx);
+      tx[k][0] = (fxm & 1 ? p.face[0] : 0) | (fxm & 2 ? p.face[1] : 0);
+      tx[k][2] = (fxp & 1 ? p.face[0] : 0) | (fxp & 2 ? p.face[1] : 0);
+      near |= (tx[k][0] | tx[k][2]) != 0;
+    }
+    near |= (ty[0] | ty[2] | tz[0] | tz[2]) != 0;
+  }
+  const int self0 = x0 + nx * row;
   float v[Q][V];
   const S* base = src;
 #pragma unroll
@@ -210,7 +256,28 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
 #pragma unroll
       for (int k = 0; k < V - 1; ++k) v[i][k] = w[k + 1];
     }
+    if (i > 0 && near) {
+      // sources on a boundary face read the own opposite population instead
+      // (lanes next to a face only; the loads join the same phase)
+      const S* own = src + (long long)opposite<Q>(i) * p.plane + self0;
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        const int t = face_combine(tx[k][1 - cx], ty[1 - Lattice<Q>::c(i, 1)], tz[1 - Lattice<Q>::c(i, 2)]);
+        if (t == WALL || t == LID) v[i][k] = Store<S>::ld(own + k);
+      }
+    }
     base += p.plane;
+  }
+  if (near) {
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        const int t = face_combine(tx[k][1 - Lattice<Q>::c(i, 0)], ty[1 - Lattice<Q>::c(i, 1)],
+                                   tz[1 - Lattice<Q>::c(i, 2)]);
+        if (t == EQ) v[i][k] = p.eq_df[i];
+        if (t == LID) v[i][k] += p.lid_term[i];
+      }
   }
 #pragma unroll
   for (int k = 0; k < V; ++k) {
@@ -415,7 +482,7 @@ int launch_typed(Op op, const LaunchArgs& a) {
       return -7;
     }
     case OP_BOUNDARY: {
-      const long long tot = a.n_links + a.n_fix;
+      const long long tot = (a.n_links + LINKS_PER_THREAD - 1) / LINKS_PER_THREAD + a.n_fix;
       if (tot <= 0) return 0;
       if (tot > 0x7fffffffLL) return -1;
       const unsigned g = (unsigned)((tot + ROW_BLOCK - 1) / ROW_BLOCK);

@@ -55,13 +55,17 @@ int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int 
                         void* stream);
 int launch_reduce_final(const double* partial, long long n, double* out, void* stream);
 
-// Boundary tables of a mask: per block of 256 cells the number of links and
-// of inlet / outlet cells (counts[2b], counts[2b+1]); then, at the exclusive
-// offsets offs[2b], offs[2b+1], the links {cell, dir | type << 8} and the
-// inlet / outlet cells, in ascending cell order.
+// Boundary tables of a mask by compaction: mode 0 selects the FLUID cells
+// whose source in direction `dir` is WALL / LID / EQ (written as links
+// {cell, dir | type << 8}), mode 1 the INLET / OUTLET cells (written to
+// `cells`).  Per block of 256 cells: counts, then ordered writes at the
+// exclusive offsets of the counts.
 long long bnd_list_blocks(long long n);
-int launch_bnd_count(int Q, const uint8_t* flags, int nx, int ny, int nz, int* counts, void* stream);
-int launch_bnd_write(int Q, const uint8_t* flags, int nx, int ny, int nz, const long long* offs, int2* links,
-                     int* fix, void* stream);
+// `face` (6 types, or null) lists the described boundary faces: links whose
+// source lies on one are left out (the pull applies those rules itself).
+int launch_pred_count(int mode, int dir, int Q, const int* face, const uint8_t* flags, int nx, int ny, int nz,
+                      int* counts, void* stream);
+int launch_pred_write(int mode, int dir, int Q, const int* face, const uint8_t* flags, int nx, int ny, int nz,
+                      const long long* offs, int2* links, int* cells, void* stream);
 
 }  // namespace xlb

@@ -43,15 +43,72 @@ __device__ __forceinline__ int src_index(const Nbr& nb, int i) {
   return nb.xo[1 - Lattice<Q>::c(i, 0)] + nb.rb[1 - Lattice<Q>::c(i, 1)][1 - Lattice<Q>::c(i, 2)];
 }
 
-// Pull without boundary rules: df_i(x) = h_i(x - c_i), periodic (Eq. 2).
+// Pull: df_i(x) = h_i(x - c_i), periodic (Eq. 2).  Sources on a boundary face
+// (StepParams::face) take the rule instead, chosen before any load so that
+// each direction is still exactly one load:
+//   WALL: h_opp(i)(x);  LID: h_opp(i)(x) + 2 w_i rho_w (c_i . u_w) / cs^2;
+//   EQ: f_i^eq(rho_w, u_w) (no load).
+// Sources elsewhere that are not fluid hold ghost values (k_boundary).
+
+// Face type of the source coordinate index k (0: v - 1, 1: v, 2: v + 1) on
+// one axis: lo / hi are the face types of coordinate 0 and n - 1.
+__device__ __forceinline__ int face_code(int v, int n) {
+  return (v == 0 ? 1 : 0) | (v == n - 1 ? 2 : 0);
+}
+
+// Source type from the three axes' face types: WALL wins, else LID / EQ.
+__device__ __forceinline__ int face_combine(int a, int b, int c) {
+  if (a == WALL || b == WALL || c == WALL) return WALL;
+  return a | b | c;  // at most one non-wall type meets (verified on the host)
+}
+
 template <int Q, typename S>
-__device__ __forceinline__ void pull_periodic(const S* __restrict__ src, long long plane, const Nbr& nb,
-                                              float (&df)[Q]) {
+__device__ __forceinline__ void pull_periodic(const S* __restrict__ src, const StepParams& p, const Nbr& nb,
+                                              int self, int x, int y, int z, float (&df)[Q]) {
+  int fcx[3] = {0, 0, 0}, fcy[3] = {0, 0, 0}, fcz[3] = {0, 0, 0};
+  bool near = false;
+  if (p.has_faces) {
+    const int xs[3] = {nb.xo[0], x, nb.xo[2]};
+    const int ys[3] = {wrap_m(y, p.ny), y, wrap_p(y, p.ny)};
+    const int zs[3] = {p.nz > 1 ? wrap_m(z, p.nz) : 0, z, p.nz > 1 ? wrap_p(z, p.nz) : 0};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int cx = face_code(xs[k], p.nx), cy = face_code(ys[k], p.ny), cz = face_code(zs[k], p.nz);
+      fcx[k] = (cx & 1 ? p.face[0] : 0) | (cx & 2 ? p.face[1] : 0);
+      fcy[k] = (cy & 1 ? p.face[2] : 0) | (cy & 2 ? p.face[3] : 0);
+      fcz[k] = p.nz > 1 ? ((cz & 1 ? p.face[4] : 0) | (cz & 2 ? p.face[5] : 0)) : 0;
+      near |= (k != 1) && (fcx[k] | fcy[k] | fcz[k]);
+    }
+  }
   const S* base = src;
+  // warp-uniform choice: a warp with no lane next to a face loads plainly;
+  // otherwise every lane picks each address branch-free, so either way the
+  // warp issues one round of Q independent loads
+  if (!__any_sync(__activemask(), near)) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      df[i] = Store<S>::ld(base + src_index<Q>(nb, i));
+      base += p.plane;
+    }
+    return;
+  }
+  // all loads first (addresses chosen branch-free), adjustments after, so
+  // the Q loads stay in flight together
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    df[i] = Store<S>::ld(base + src_index<Q>(nb, i));
-    base += plane;
+    const int t = i == 0 ? 0
+                         : face_combine(fcx[1 - Lattice<Q>::c(i, 0)], fcy[1 - Lattice<Q>::c(i, 1)],
+                                        fcz[1 - Lattice<Q>::c(i, 2)]);
+    const S* a = t ? src + (long long)opposite<Q>(i) * p.plane + self : base + src_index<Q>(nb, i);
+    df[i] = Store<S>::ld(a);
+    base += p.plane;
+  }
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int t = face_combine(fcx[1 - Lattice<Q>::c(i, 0)], fcy[1 - Lattice<Q>::c(i, 1)],
+                               fcz[1 - Lattice<Q>::c(i, 2)]);
+    if (t == EQ) df[i] = p.eq_df[i];
+    if (t == LID) df[i] += p.lid_term[i];
   }
 }
 
@@ -78,22 +135,24 @@ __device__ __forceinline__ void zou_he_inlet(const StepParams& p, float (&df)[Q]
   }
 }
 
-// Post-stream populations of a fluid-like cell.  The stored state carries
-// ghost values in every WALL / LID / EQ cell (see k_boundary), so the
-// periodic pull already applies the bounce-back, moving-wall and equilibrium
+// Post-stream populations of a fluid-like cell.  The pull applies the face
+// rules and reads the ghost values that every other WALL / LID / EQ source
+// carries (see k_boundary), i.e. the bounce-back, moving-wall and equilibrium
 // rules; INLET cells then rebuild their c_x = +1 populations by Zou-He and
 // OUTLET cells copy their c_x = -1 populations from the pull at x - 1
 // (zero-gradient outflow).
 template <int Q, typename S>
 __device__ __forceinline__ void pull_cell(const S* __restrict__ src, const StepParams& p, int x, int y, int z,
                                           int type, const Nbr& nb, float (&df)[Q]) {
-  pull_periodic<Q, S>(src, p.plane, nb, df);
+  const int self = x + p.nx * (y + p.ny * z);
+  pull_periodic<Q, S>(src, p, nb, self, x, y, z, df);
   if (type == INLET) zou_he_inlet<Q>(p, df);
   if (type == OUTLET) {
+    const int xl = wrap_m(x, p.nx);
     Nbr nl;
-    make_nbr(nl, wrap_m(x, p.nx), y, z, p.nx, p.ny, p.nz);
+    make_nbr(nl, xl, y, z, p.nx, p.ny, p.nz);
     float dl[Q];
-    pull_periodic<Q, S>(src, p.plane, nl, dl);
+    pull_periodic<Q, S>(src, p, nl, self - x + xl, xl, y, z, dl);
 #pragma unroll
     for (int i = 0; i < Q; ++i)
       if (Lattice<Q>::c(i, 0) == -1) df[i] = dl[i];

@@ -64,128 +64,123 @@ int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int 
   return 0;
 }
 
-// Boundary tables, built once per mask in two passes (per-block counts, an
-// exclusive scan of the counts on the host, then ordered per-block writes):
-//  - links: one entry per (fluid cell x, direction i) whose source cell
-//    x - c_i is WALL, LID or EQ, packed as {x, i | type << 8};
-//  - fix-up cells: every INLET and OUTLET cell.
+// Boundary tables, built once per mask by compaction in two passes per
+// table (per-block counts; an exclusive scan of the counts on the host; then
+// ordered per-block writes):
+//  - links, direction-major: for each direction i in turn, every FLUID cell x
+//    (ascending) whose source x - c_i is WALL, LID or EQ, as {x, i | type << 8}.
+//    Consecutive entries then touch consecutive cells of one population
+//    plane wherever the wall is not normal to x;
+//  - fix-up cells: every INLET and OUTLET cell, ascending.
 constexpr int LIST_BLOCK = 256;
 
-template <int Q>
-__device__ __forceinline__ int cell_links(const uint8_t* __restrict__ mask, long long cell, int nx, int ny, int nz,
-                                          int* types /* Q or null */) {
+struct Pred {
+  int mode;        // 0: link in direction (cx, cy, cz); 1: inlet / outlet cell
+  int cx, cy, cz;  // velocity of the link direction
+  int face[6];     // described boundary faces: their sources need no ghost
+};
+
+__device__ __forceinline__ int pred_eval(const uint8_t* __restrict__ flags, long long cell, int nx, int ny, int nz,
+                                         const Pred& pr, int* type) {
+  const int t = flags[cell] & FLAG_TYPE;
+  if (pr.mode == 1) return t == INLET || t == OUTLET;
+  if (t != FLUID) return 0;
   const int x = (int)(cell % nx);
   const long long r = cell / nx;
   const int y = (int)(r % ny), z = (int)(r / ny);
-  int n = 0;
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    int xs = x - Lattice<Q>::c(i, 0), ys = y - Lattice<Q>::c(i, 1), zs = z - Lattice<Q>::c(i, 2);
-    xs = xs < 0 ? nx - 1 : (xs >= nx ? 0 : xs);
-    ys = ys < 0 ? ny - 1 : (ys >= ny ? 0 : ys);
-    zs = zs < 0 ? nz - 1 : (zs >= nz ? 0 : zs);
-    const int t = mask[xs + (long long)nx * (ys + (long long)ny * zs)] & FLAG_TYPE;
-    const bool link = !fluid_like(t);
-    if (types) types[i] = link ? t : 0;
-    n += link;
-  }
-  return n;
+  int xs = x - pr.cx, ys = y - pr.cy, zs = z - pr.cz;
+  xs = xs < 0 ? nx - 1 : (xs >= nx ? 0 : xs);
+  ys = ys < 0 ? ny - 1 : (ys >= ny ? 0 : ys);
+  zs = zs < 0 ? nz - 1 : (zs >= nz ? 0 : zs);
+  const int ts = flags[xs + (long long)nx * (ys + (long long)ny * zs)] & FLAG_TYPE;
+  *type = ts;
+  const bool on_face = (xs == 0 && pr.face[0]) || (xs == nx - 1 && pr.face[1]) || (ys == 0 && pr.face[2]) ||
+                       (ys == ny - 1 && pr.face[3]) || (nz > 1 && zs == 0 && pr.face[4]) ||
+                       (nz > 1 && zs == nz - 1 && pr.face[5]);
+  return !fluid_like(ts) && !on_face;
 }
 
-// Block-wide exclusive scan of one int per thread (LIST_BLOCK threads).
-__device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
-  __shared__ int warp_sums[LIST_BLOCK / 32];
+__global__ void k_pred_count(const uint8_t* __restrict__ flags, long long n, int nx, int ny, int nz, Pred pr,
+                             int* counts) {
+  const long long cell = blockIdx.x * (long long)LIST_BLOCK + threadIdx.x;
+  int t = 0;
+  const int hit = cell < n ? pred_eval(flags, cell, nx, ny, nz, pr, &t) : 0;
+  const int c = __syncthreads_count(hit);
+  if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+
+__global__ void k_pred_write(const uint8_t* __restrict__ flags, long long n, int nx, int ny, int nz, Pred pr,
+                             int dir, const long long* __restrict__ offs, int2* links, int* cells) {
+  __shared__ int warp_base[LIST_BLOCK / 32];
+  const long long cell = blockIdx.x * (long long)LIST_BLOCK + threadIdx.x;
+  int t = 0;
+  const int hit = cell < n ? pred_eval(flags, cell, nx, ny, nz, pr, &t) : 0;
+  const unsigned ballot = __ballot_sync(0xffffffffu, hit);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int u = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += u;
-  }
-  if (lane == 31) warp_sums[warp] = incl;
+  if (lane == 0) warp_base[warp] = __popc(ballot);
   __syncthreads();
   if (threadIdx.x == 0) {
     int run = 0;
     for (int w = 0; w < LIST_BLOCK / 32; ++w) {
-      const int c = warp_sums[w];
-      warp_sums[w] = run;
+      const int c = warp_base[w];
+      warp_base[w] = run;
       run += c;
     }
-    *total = run;
   }
   __syncthreads();
-  return warp_sums[warp] + incl - v;
-}
-
-template <int Q>
-__global__ void k_bnd_count(const uint8_t* __restrict__ flags, long long n, int nx, int ny, int nz, int* counts) {
-  const long long cell = blockIdx.x * (long long)LIST_BLOCK + threadIdx.x;
-  int nl = 0, nf = 0;
-  if (cell < n) {
-    const int t = flags[cell] & FLAG_TYPE;
-    if (t == FLUID && (flags[cell] & FLAG_SLOW)) nl = cell_links<Q>(flags, cell, nx, ny, nz, nullptr);
-    nf = (t == INLET || t == OUTLET);
+  if (hit) {
+    const long long o = offs[blockIdx.x] + warp_base[warp] + __popc(ballot & ((1u << lane) - 1u));
+    if (pr.mode == 1)
+      cells[o] = (int)cell;
+    else
+      links[o] = make_int2((int)cell, dir | (t << 8));
   }
-  __shared__ int tl, tf;
-  block_exclusive_scan(nl, &tl);
-  block_exclusive_scan(nf, &tf);
-  if (threadIdx.x == 0) {
-    counts[2 * blockIdx.x] = tl;
-    counts[2 * blockIdx.x + 1] = tf;
-  }
-}
-
-template <int Q>
-__global__ void k_bnd_write(const uint8_t* __restrict__ flags, long long n, int nx, int ny, int nz,
-                            const long long* __restrict__ offs, int2* links, int* fix) {
-  const long long cell = blockIdx.x * (long long)LIST_BLOCK + threadIdx.x;
-  int nl = 0, nf = 0;
-  int types[Q];
-  if (cell < n) {
-    const int t = flags[cell] & FLAG_TYPE;
-    if (t == FLUID && (flags[cell] & FLAG_SLOW)) nl = cell_links<Q>(flags, cell, nx, ny, nz, types);
-    nf = (t == INLET || t == OUTLET);
-  }
-  __shared__ int tl, tf;
-  const int pl = block_exclusive_scan(nl, &tl);
-  const int pf = block_exclusive_scan(nf, &tf);
-  if (nl) {
-    long long o = offs[2 * blockIdx.x] + pl;
-#pragma unroll
-    for (int i = 1; i < Q; ++i)
-      if (types[i]) links[o++] = make_int2((int)cell, i | (types[i] << 8));
-  }
-  if (nf) fix[offs[2 * blockIdx.x + 1] + pf] = (int)cell;
 }
 
 long long bnd_list_blocks(long long n) { return (n + LIST_BLOCK - 1) / LIST_BLOCK; }
 
-int launch_bnd_count(int Q, const uint8_t* flags, int nx, int ny, int nz, int* counts, void* stream) {
+static Pred make_pred(int mode, int dir, int Q, const int* face) {
+  Pred pr;
+  pr.mode = mode;
+  pr.cx = pr.cy = pr.cz = 0;
+  for (int f = 0; f < 6; ++f) pr.face[f] = face ? face[f] : 0;
+  if (mode == 0) {
+    if (Q == 9) {
+      pr.cx = Lattice<9>::c(dir, 0);
+      pr.cy = Lattice<9>::c(dir, 1);
+    }
+    if (Q == 19) {
+      pr.cx = Lattice<19>::c(dir, 0);
+      pr.cy = Lattice<19>::c(dir, 1);
+      pr.cz = Lattice<19>::c(dir, 2);
+    }
+    if (Q == 27) {
+      pr.cx = Lattice<27>::c(dir, 0);
+      pr.cy = Lattice<27>::c(dir, 1);
+      pr.cz = Lattice<27>::c(dir, 2);
+    }
+  }
+  return pr;
+}
+
+int launch_pred_count(int mode, int dir, int Q, const int* face, const uint8_t* flags, int nx, int ny, int nz,
+                      int* counts, void* stream) {
   const long long n = (long long)nx * ny * nz;
   const long long b = bnd_list_blocks(n);
-  cudaStream_t s = (cudaStream_t)stream;
   if (b > 0x7fffffffLL) return -1;
-  if (Q == 9)
-    k_bnd_count<9><<<(unsigned)b, LIST_BLOCK, 0, s>>>(flags, n, nx, ny, nz, counts);
-  else if (Q == 19)
-    k_bnd_count<19><<<(unsigned)b, LIST_BLOCK, 0, s>>>(flags, n, nx, ny, nz, counts);
-  else
-    k_bnd_count<27><<<(unsigned)b, LIST_BLOCK, 0, s>>>(flags, n, nx, ny, nz, counts);
+  const Pred pr = make_pred(mode, dir, Q, face);
+  k_pred_count<<<(unsigned)b, LIST_BLOCK, 0, (cudaStream_t)stream>>>(flags, n, nx, ny, nz, pr, counts);
   return 0;
 }
 
-int launch_bnd_write(int Q, const uint8_t* flags, int nx, int ny, int nz, const long long* offs, int2* links,
-                     int* fix, void* stream) {
+int launch_pred_write(int mode, int dir, int Q, const int* face, const uint8_t* flags, int nx, int ny, int nz,
+                      const long long* offs, int2* links, int* cells, void* stream) {
   const long long n = (long long)nx * ny * nz;
   const long long b = bnd_list_blocks(n);
-  cudaStream_t s = (cudaStream_t)stream;
   if (b > 0x7fffffffLL) return -1;
-  if (Q == 9)
-    k_bnd_write<9><<<(unsigned)b, LIST_BLOCK, 0, s>>>(flags, n, nx, ny, nz, offs, links, fix);
-  else if (Q == 19)
-    k_bnd_write<19><<<(unsigned)b, LIST_BLOCK, 0, s>>>(flags, n, nx, ny, nz, offs, links, fix);
-  else
-    k_bnd_write<27><<<(unsigned)b, LIST_BLOCK, 0, s>>>(flags, n, nx, ny, nz, offs, links, fix);
+  const Pred pr = make_pred(mode, dir, Q, face);
+  k_pred_write<<<(unsigned)b, LIST_BLOCK, 0, (cudaStream_t)stream>>>(flags, n, nx, ny, nz, pr, dir, offs, links,
+                                                                     cells);
   return 0;
 }
 

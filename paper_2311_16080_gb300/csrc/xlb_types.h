@@ -37,6 +37,12 @@ struct StepParams {
   float eq_rho, eq_u[3];
   float inlet_u[3];      // Zou-He inlet velocity
   int* err;              // device error word for kernels with bounded waits
+  // Boundary faces: type (0 = none, WALL, LID or EQ) of each whole face plane
+  // x = 0, x = nx-1, y = 0, y = ny-1, z = 0, z = nz-1 that the mask fills
+  // uniformly (WALL wins where planes meet).  Pulls from such a plane apply
+  // the rule by coordinates; every other non-fluid source uses ghost values.
+  int face[6];
+  int has_faces;
 };
 
 // Device error codes written to StepParams::err.

@@ -71,31 +71,74 @@ def test_auto_picks_vec_for_16_bit_storage_only():
     s32 = c.gpu_sim("f32")
     s16 = c.gpu_sim("f16")
     assert s32.kernel() == X.XLB_KERNEL_DIRECT
-    assert s16.kernel() == X.XLB_KERNEL_VEC
+    assert s16.kernel() == X.XLB_KERNEL_DIRECT  # the cavity's walls are faces
+    per16 = Case(19, (8, 8, 32), 1.5, "bgk").gpu_sim("f16")
+    assert per16.kernel() == X.XLB_KERNEL_VEC
     with pytest.raises(X.XlbError) as e:
         X.xlb_set_kernel(s32.ctx, X.XLB_KERNEL_VEC)
     assert e.value.status == X.XLB_ERR_UNSUPPORTED
     odd = Case(9, (30, 45), 1.2).gpu_sim("f16")
     assert odd.kernel() == X.XLB_KERNEL_DIRECT  # nx % 4 != 0
-    for s in (s32, s16, odd):
+    for s in (s32, s16, odd, per16):
         s.close()
+
+
+def _links(q, m, skip_faces=()):
+    lat = O.Lattice(q)
+    n = 0
+    for i in range(1, q):
+        src_nonfluid = ~O.fluid_like(lat.roll(m, i))
+        on_face = np.zeros(m.shape, bool)
+        for ax, side in skip_faces:  # ax in array-axis order, side 0 / -1
+            idx = [slice(None)] * m.ndim
+            coord = np.arange(m.shape[ax])
+            shift = int(lat.c[i][::-1][ax])
+            src_coord = (coord - shift) % m.shape[ax]
+            hit = src_coord == (0 if side == 0 else m.shape[ax] - 1)
+            sh = [1] * m.ndim
+            sh[ax] = m.shape[ax]
+            on_face |= hit.reshape(sh)
+        n += int(((m == O.FLUID) & src_nonfluid & ~on_face).sum())
+    return n
 
 
 def test_boundary_tables():
-    """One ghost link per (fluid cell, direction) whose source is WALL, LID or
-    EQ, and one fix-up entry per inlet / outlet cell."""
-    for q, m in ((19, I.lid_driven_cavity_mask(20, 18, 16)),
-                 (27, I.sphere_channel_mask(40, 16, 12, radius=3, center=(12, 8, 6))),
-                 (9, np.where(I.random_obstacle_mask((30, 40), 0.1, seed=2) > 0, O.EQ, 0).astype(np.uint8))):
-        lat = O.Lattice(q)
-        links = 0
-        for i in range(1, q):
-            links += int(((m == O.FLUID) & ~O.fluid_like(lat.roll(m, i))).sum())
-        fix = int(np.isin(m, (O.INLET, O.OUTLET)).sum())
+    """Ghost links: one per (fluid cell, direction) whose source is WALL, LID
+    or EQ and not on a boundary face plane the mask fills uniformly (those the
+    pull handles by coordinates); one fix-up entry per inlet / outlet cell."""
+    cav = I.lid_driven_cavity_mask(20, 18, 16)
+    holed = cav.copy()
+    holed[5:8, 6:9, 0] = O.FLUID  # x = 0 plane no longer a face
+    sph = I.sphere_channel_mask(40, 16, 12, radius=3, center=(12, 8, 6))
+    eqs = np.where(I.random_obstacle_mask((30, 40), 0.1, seed=2) > 0, O.EQ, 0).astype(np.uint8)
+    all_faces = [(2, 0), (2, -1), (1, 0), (1, -1), (0, 0), (0, -1)]
+    # the hole removes the x = 0 face; the lid plane's x = 0 edge cells are
+    # WALL, which only the x = 0 face explained, so the lid face goes too
+    holed_faces = [f for f in all_faces if f not in ((2, 0), (0, -1))]
+    for q, m, faces in ((19, cav, all_faces), (19, holed, holed_faces),
+                        (27, sph, []), (9, eqs, [])):
+        want = (_links(q, m, faces), int(np.isin(m, (O.INLET, O.OUTLET)).sum()))
         s = X.Simulation(q, tuple(reversed(m.shape)), 1.5, "bgk")
         s.set_mask(m)
-        assert X.xlb_boundary_links(s.ctx) == (links, fix)
+        assert X.xlb_boundary_links(s.ctx) == want
         s.close()
+    assert _links(19, cav, all_faces) == 0
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_faces_and_ghosts_mixed_parity(storage):
+    """A cavity whose x = 0 wall has a hole (no longer a face: ghost links),
+    an EQ top face, interior obstacles: against the oracle."""
+    m = I.lid_driven_cavity_mask(32, 20, 18)
+    m[m == O.LID] = O.EQ
+    m[6:10, 5:9, 0] = O.FLUID
+    m[I.random_obstacle_mask(m.shape, 0.03, seed=9) > 0] = O.WALL
+    rho, u = I.random_flow(m.shape, 3, seed=10, rho_amp=0.005, u_amp=0.02)
+    c = Case(19, m.shape, 1.6, "bgk", mask=m, eq=(1.0, (0.03, 0.0, 0.0)), rho0=rho, u0=u)
+    (rho_o, u_o), _ = c.oracle(100)
+    rho_g, u_g = c.gpu(100, storage)
+    fl = O.fluid_like(m)
+    assert rel_l2(u_g[:, fl], u_o[:, fl]) <= (1e-4 if storage == "f32" else 5e-3)
 
 
 def test_ghosts_follow_lid_and_mask_changes():
