@@ -214,8 +214,13 @@ int xlb_adjoint_step(xlb_ctx* ctx, int64_t n);
  * may be NULL.  Solid and EQ cells get 0. */
 int xlb_adjoint_init_grad(xlb_ctx* ctx, float* dL_drho0, float* dL_du0);
 
-/* Free the tape, checkpoints and adjoint buffers. */
+/* Close the tape.  Its memory (checkpoints, tape slots, adjoint buffers) is
+ * kept for the next tape of the same or smaller size, so repeated gradients
+ * allocate nothing after the first. */
 int xlb_tape_end(xlb_ctx* ctx);
+
+/* Close the tape and free its memory. */
+int xlb_tape_release(xlb_ctx* ctx);
 
 /* ---- kernel selection -------------------------------------------------- */
 

@@ -68,8 +68,10 @@ struct xlb_ctx {
   // tape / adjoint
   bool tape_open = false;
   int64_t tape_T = 0, tape_k = 0;
-  std::vector<void*> ckpt;
+  std::vector<void*> ckpt;   // views into the tape arena
   std::vector<void*> slots;
+  char* tape_arena = nullptr;  // checkpoints, tape slots and adjoint buffers, kept for reuse
+  size_t tape_arena_bytes = 0;
   int64_t seg_loaded = -1;
   float* abar[2] = {nullptr, nullptr};
   int acur = 0;
@@ -486,9 +488,11 @@ int xlb_create(xlb_ctx** out, int lattice, const int64_t dims[3], double omega, 
 
 int xlb_tape_end(xlb_ctx* c);
 
+int xlb_tape_release(xlb_ctx* c);
+
 void xlb_destroy(xlb_ctx* c) {
   if (!c) return;
-  xlb_tape_end(c);
+  xlb_tape_release(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (int k = 0; k < 2; ++k)
     if (c->buf[k]) cudaFree(c->buf[k]);
@@ -871,20 +875,27 @@ int xlb_populations(xlb_ctx* c, void** ptr, int64_t* plane) {
 // ---------------------------------------------------------------------------
 // reverse mode
 
+// The tape memory (checkpoints, k tape slots, two FP32 adjoint buffers) is one
+// arena that outlives xlb_tape_end, so repeated gradients do not allocate; it
+// grows when a larger tape needs it and is freed by xlb_tape_release.
 int xlb_tape_end(xlb_ctx* c) {
   if (!c) return XLB_ERR_ARG;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (void* p : c->ckpt) cudaFree(p);
-  for (void* p : c->slots) cudaFree(p);
   c->ckpt.clear();
   c->slots.clear();
-  for (int k = 0; k < 2; ++k) {
-    if (c->abar[k]) cudaFree(c->abar[k]);
-    c->abar[k] = nullptr;
-  }
+  c->abar[0] = c->abar[1] = nullptr;
   c->tape_open = false;
   c->seg_loaded = -1;
   c->adj_t = -1;
+  return XLB_OK;
+}
+
+int xlb_tape_release(xlb_ctx* c) {
+  if (!c) return XLB_ERR_ARG;
+  xlb_tape_end(c);
+  if (c->tape_arena) cudaFree(c->tape_arena);
+  c->tape_arena = nullptr;
+  c->tape_arena_bytes = 0;
   return XLB_OK;
 }
 
@@ -897,35 +908,32 @@ int xlb_tape_begin(xlb_ctx* c, int64_t n_steps, int64_t k) {
   xlb_tape_end(c);
   if (k > n_steps) k = n_steps;
   const int64_t n_ckpt = (n_steps - 1) / k;
-  const size_t sb = state_bytes_raw(c);
-  for (int64_t s = 0; s < n_ckpt; ++s) {
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, sb);
+  const size_t sb = (state_bytes_raw(c) + 255) / 256 * 256;
+  const size_t ab = (sizeof(float) * state_elems(c) + 255) / 256 * 256;
+  const size_t need = (size_t)(n_ckpt + k) * sb + 2 * ab;
+  if (c->tape_arena_bytes < need) {
+    if (c->tape_arena) cudaFree(c->tape_arena);
+    c->tape_arena = nullptr;
+    c->tape_arena_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->tape_arena, need);
     if (e != cudaSuccess) {
-      xlb_tape_end(c);
-      return cuda_fail(c, e, "cudaMalloc(checkpoint)");
+      c->tape_arena = nullptr;
+      return cuda_fail(c, e, "cudaMalloc(tape)");
     }
-    c->ckpt.push_back(p);
+    c->tape_arena_bytes = need;
   }
+  char* p = c->tape_arena;
+  for (int64_t s = 0; s < n_ckpt; ++s, p += sb) c->ckpt.push_back(p);
+  for (int64_t j = 0; j < k; ++j, p += sb) c->slots.push_back(p);
+  c->abar[0] = reinterpret_cast<float*>(p);
+  c->abar[1] = reinterpret_cast<float*>(p + ab);
   c->tape_open = true;
   c->tape_T = n_steps;
   c->tape_k = k;
   return XLB_OK;
 }
 
-static int ensure_adjoint_buffers(xlb_ctx* c) {
-  const size_t ab = sizeof(float) * state_elems(c);
-  for (int k = 0; k < 2; ++k)
-    if (!c->abar[k]) CK(cudaMalloc(&c->abar[k], ab));
-  if (c->slots.empty()) {
-    for (int64_t j = 0; j < c->tape_k; ++j) {
-      void* p = nullptr;
-      CK(cudaMalloc(&p, state_bytes_raw(c)));
-      c->slots.push_back(p);
-    }
-  }
-  return XLB_OK;
-}
+static int ensure_adjoint_buffers(xlb_ctx* c) { return c->tape_open ? XLB_OK : XLB_ERR_STATE; }
 
 static AdjointArgs adjoint_args(xlb_ctx* c) {
   AdjointArgs a;

@@ -66,6 +66,7 @@ _PROTOS = {
     "xlb_adjoint_step": (_i, [_vp, _i64]),
     "xlb_adjoint_init_grad": (_i, [_vp, _vp, _vp]),
     "xlb_tape_end": (_i, [_vp]),
+    "xlb_tape_release": (_i, [_vp]),
     "xlb_set_kernel": (_i, [_vp, _i]),
     "xlb_get_kernel": (_i, [_vp, C.POINTER(_i)]),
     "xlb_profile_enable": (_i, [_vp, _i]),
@@ -257,6 +258,10 @@ def xlb_adjoint_init_grad(ctx, dL_drho0=None, dL_du0=None):
 
 def xlb_tape_end(ctx):
     _check(load().xlb_tape_end(ctx), ctx)
+
+
+def xlb_tape_release(ctx):
+    _check(load().xlb_tape_release(ctx), ctx)
 
 
 def xlb_set_kernel(ctx, variant=XLB_KERNEL_AUTO):

@@ -102,6 +102,37 @@ def test_adjoint_matches_central_differences():
         assert abs(float((g_rho * d).sum()) - fd) <= 1e-3 * abs(fd)
 
 
+def test_repeated_gradients_reuse_the_tape():
+    """Two gradients in a row on one context (the second reuses the tape
+    memory kept after xlb_tape_end) are identical; a larger tape afterwards
+    grows the memory and still matches a fresh context."""
+    c = _case(9, (24, 32), True, None)
+    sim = c.gpu_sim()
+    box = _box(c.shape)
+
+    def grad(steps, k):
+        sim.init(np.ascontiguousarray(c.rho0, dtype=np.float32), np.ascontiguousarray(c.u0, dtype=np.float32))
+        X.xlb_tape_begin(sim.ctx, steps, k)
+        sim.step(steps)
+        rho, u = sim.macroscopic()
+        rb, ub = O.kinetic_energy_grads(rho.astype(np.float64), u.astype(np.float64), box)
+        X.xlb_adjoint_seed_macro(sim.ctx, rb.astype(np.float32), ub.astype(np.float32))
+        X.xlb_adjoint_step(sim.ctx, steps)
+        g = np.empty(c.shape, np.float32)
+        X.xlb_adjoint_init_grad(sim.ctx, g, None)
+        X.xlb_tape_end(sim.ctx)
+        return g
+
+    a = grad(30, 5)
+    b = grad(30, 5)
+    assert np.array_equal(a, b)
+    big = grad(50, 10)
+    X.xlb_tape_release(sim.ctx)
+    sim.close()
+    fresh, _ = gpu_gradient(c, 50, 10)
+    assert np.array_equal(big, fresh)
+
+
 def test_adjoint_state_errors():
     c = _case(9, (16, 16), False, None)
     sim = c.gpu_sim()
