@@ -323,6 +323,39 @@ def extras(args, torch, X, I, stream):
     res["adjoint_d3q19_128_gradient_rollout_mlups"] = round(500 * cells / (grad_s * 1e6), 1)
     res["adjoint_grad_norm"] = float(torch.linalg.vector_norm(g.double()).item())
 
+    # batched channels: 4096 D2Q9 domains (32..256 x 32..128, 1-5 discs, body
+    # force), autotuned launch shape, 5000 steps in one persistent CUDA-graph
+    # launch; the launch-per-domain baseline runs 50 steps (extrapolated)
+    doms = I.batched_channels(4096, seed=1234, nu=(1.0 / 1.25 - 0.5) / 3.0, u_max=0.05)
+    bt = X.Batch(doms, 1.25, "f32", stream=stream.cuda_stream)
+    bt.set_masks()
+    bt.init()
+    bt.step(2)
+    th, ct = bt.tune(20)
+    cells = sum(bt.cells)
+    a, b2 = ev(), ev()
+    bt.step(10)
+    torch.cuda.synchronize()
+    a.record(stream)
+    bt.step(5000)
+    b2.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b2)
+    res["batch4096_cells"] = cells
+    res["batch4096_launch"] = {"threads": th, "ctas_per_sm": ct}
+    res["batch4096_persistent_mlups"] = round(cells * 5000 / (ms * 1e3), 1)
+    res["batch4096_persistent_algo_GBs"] = round(72 * cells * 5000 / (ms * 1e-3) / 1e9, 1)
+    a, b2 = ev(), ev()
+    a.record(stream)
+    bt.step_per_domain(50)
+    b2.record(stream)
+    torch.cuda.synchronize()
+    ms_pd = a.elapsed_time(b2)
+    res["batch4096_per_domain_mlups_50_steps"] = round(cells * 50 / (ms_pd * 1e3), 1)
+    res["batch4096_per_domain_5000_steps_s_extrapolated"] = round(ms_pd / 50 * 5000 / 1e3, 2)
+    res["batch4096_persistent_5000_steps_s"] = round(ms / 1e3, 3)
+    bt.close()
+
     # storage error: Taylor-Green 128^2, 1000 steps, against the FP64 oracle
     try:
         from oracle import lbm as O

@@ -241,6 +241,55 @@ int xlb_set_kernel(xlb_ctx* ctx, int variant);
 /* The variant the next update launches (DIRECT or VEC). */
 int xlb_get_kernel(const xlb_ctx* ctx, int* variant);
 
+/* ---- batched small 2D domains (Section 6 batching) --------------------- */
+
+typedef struct xlb_batch xlb_batch;
+
+/* n_domains independent D2Q9 BGK domains of nx[d] x ny[d] cells (each at
+ * most 2^26 cells, all together at most 2^31 - 1), relaxation omega, storage
+ * XLB_STORE_*.  Every domain is periodic in x and y unless its mask says
+ * otherwise.  The library owns all buffers. */
+int xlb_batch_create(xlb_batch** out, int n_domains, const int32_t* nx, const int32_t* ny, double omega,
+                     int storage, void* cuda_stream);
+void xlb_batch_destroy(xlb_batch* b);
+const char* xlb_batch_last_error(const xlb_batch* b);
+
+/* Cell masks (concatenated per domain, each x fastest; FLUID or WALL codes
+ * only, XLB_ERR_UNSUPPORTED otherwise) and body forces (2 floats per domain,
+ * exact-difference forcing); either may be NULL to keep the current one.
+ * Host or device memory. */
+int xlb_batch_set_masks(xlb_batch* b, const uint8_t* masks, const float* forces);
+
+/* f_0 = f^eq(rho, u) per cell: rho (total cells) and u (2 per cell,
+ * interleaved u_x, u_y) concatenated like the masks, or NULL (1 and 0). */
+int xlb_batch_init(xlb_batch* b, const float* rho, const float* u);
+
+/* Advance every domain n steps in one persistent launch: each CTA takes
+ * domains from a queue, largest first, and runs all n steps of one domain
+ * before the next.  The launch is captured in a CUDA graph on first use and
+ * replayed while n and the launch shape stay the same. */
+int xlb_batch_step(xlb_batch* b, int64_t n);
+
+/* The same n steps with one ordinary launch per domain and step (the
+ * baseline the persistent launch replaces). */
+int xlb_batch_step_per_domain(xlb_batch* b, int64_t n);
+
+/* Launch shape of xlb_batch_step: threads per CTA (32..1024, a multiple of
+ * 32) and resident CTAs per SM (1..32, capped by occupancy). */
+int xlb_batch_set_launch(xlb_batch* b, int threads, int ctas_per_sm);
+
+/* Autotuner: time every candidate shape over sample_steps updates on a saved
+ * copy of the state (restored afterwards), keep the fastest, append it to the
+ * cache file (NULL: no cache; a matching line skips the timing). */
+int xlb_batch_tune(xlb_batch* b, int sample_steps, const char* cache_path, int* best_threads, int* best_ctas);
+
+/* rho (total cells) and u (2 per cell) of every domain's post-stream state;
+ * reported u = (j + F/2) / rho; WALL cells 0.  Host or device; synchronises. */
+int xlb_batch_macroscopic(xlb_batch* b, float* rho, float* u);
+
+int xlb_batch_info(const xlb_batch* b, int64_t* total_cells, int64_t* t, int* threads, int* ctas_per_sm);
+int xlb_batch_synchronize(xlb_batch* b);
+
 /* ---- timing of the hot kernels ----------------------------------------- */
 
 /* Total device time in ms of the launches of one kernel class recorded

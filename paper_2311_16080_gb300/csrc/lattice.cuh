@@ -99,9 +99,13 @@ __host__ __device__ constexpr int opposite(int i) {
 template <typename S>
 struct Store;
 
+// ld_l2 / st_l2: coherent at L2 (bypass L1), for data written earlier in the
+// same kernel by other threads of the block.
 template <>
 struct Store<float> {
   __device__ __forceinline__ static float ld(const float* p) { return __ldg(p); }
+  __device__ __forceinline__ static float ld_l2(const float* p) { return __ldcg(p); }
+  __device__ __forceinline__ static void st_l2(float* p, float v) { __stcg(p, v); }
   __device__ __forceinline__ static float ld_plain(const float* p) { return *p; }
   __device__ __forceinline__ static void st(float* p, float v) { *p = v; }
   __device__ __forceinline__ static void st_stream(float* p, float v) { __stcs(p, v); }
@@ -110,6 +114,8 @@ struct Store<float> {
 template <>
 struct Store<__half> {
   __device__ __forceinline__ static float ld(const __half* p) { return __half2float(__ldg(p)); }
+  __device__ __forceinline__ static float ld_l2(const __half* p) { return __half2float(__ldcg(p)); }
+  __device__ __forceinline__ static void st_l2(__half* p, float v) { __stcg(p, __float2half_rn(v)); }
   __device__ __forceinline__ static float ld_plain(const __half* p) { return __half2float(*p); }
   __device__ __forceinline__ static void st(__half* p, float v) { *p = __float2half_rn(v); }
   __device__ __forceinline__ static void st_stream(__half* p, float v) { __stcs(p, __float2half_rn(v)); }
@@ -118,6 +124,8 @@ struct Store<__half> {
 template <>
 struct Store<__nv_bfloat16> {
   __device__ __forceinline__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+  __device__ __forceinline__ static float ld_l2(const __nv_bfloat16* p) { return __bfloat162float(__ldcg(p)); }
+  __device__ __forceinline__ static void st_l2(__nv_bfloat16* p, float v) { __stcg(p, __float2bfloat16_rn(v)); }
   __device__ __forceinline__ static float ld_plain(const __nv_bfloat16* p) { return __bfloat162float(*p); }
   __device__ __forceinline__ static void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
   __device__ __forceinline__ static void st_stream(__nv_bfloat16* p, float v) {

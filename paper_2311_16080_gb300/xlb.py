@@ -69,6 +69,18 @@ _PROTOS = {
     "xlb_tape_release": (_i, [_vp]),
     "xlb_set_kernel": (_i, [_vp, _i]),
     "xlb_get_kernel": (_i, [_vp, C.POINTER(_i)]),
+    "xlb_batch_create": (_i, [C.POINTER(_vp), _i, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _d, _i, _vp]),
+    "xlb_batch_destroy": (None, [_vp]),
+    "xlb_batch_last_error": (C.c_char_p, [_vp]),
+    "xlb_batch_set_masks": (_i, [_vp, _vp, _vp]),
+    "xlb_batch_init": (_i, [_vp, _vp, _vp]),
+    "xlb_batch_step": (_i, [_vp, _i64]),
+    "xlb_batch_step_per_domain": (_i, [_vp, _i64]),
+    "xlb_batch_set_launch": (_i, [_vp, _i, _i]),
+    "xlb_batch_tune": (_i, [_vp, _i, C.c_char_p, C.POINTER(_i), C.POINTER(_i)]),
+    "xlb_batch_macroscopic": (_i, [_vp, _vp, _vp]),
+    "xlb_batch_info": (_i, [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i), C.POINTER(_i)]),
+    "xlb_batch_synchronize": (_i, [_vp]),
     "xlb_profile_enable": (_i, [_vp, _i]),
     "xlb_profile_read": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_i64)]),
 }
@@ -285,6 +297,65 @@ def xlb_profile_read(ctx, kernel=0):
     return ms.value, n.value
 
 
+def _bcheck(status, b):
+    if status != XLB_OK:
+        raise XlbError(status, load().xlb_batch_last_error(b).decode(errors="replace"))
+
+
+def xlb_batch_create(nx, ny, omega, storage=XLB_STORE_F32, cuda_stream=None):
+    out = C.c_void_p()
+    n = len(nx)
+    ax = (C.c_int32 * n)(*[int(v) for v in nx])
+    ay = (C.c_int32 * n)(*[int(v) for v in ny])
+    _bcheck(load().xlb_batch_create(C.byref(out), n, ax, ay, float(omega), int(storage), cuda_stream), None)
+    return out.value
+
+
+def xlb_batch_destroy(b):
+    load().xlb_batch_destroy(b)
+
+
+def xlb_batch_set_masks(b, masks=None, forces=None):
+    _bcheck(load().xlb_batch_set_masks(b, _ptr(masks), _ptr(forces)), b)
+
+
+def xlb_batch_init(b, rho=None, u=None):
+    _bcheck(load().xlb_batch_init(b, _ptr(rho), _ptr(u)), b)
+
+
+def xlb_batch_step(b, n):
+    _bcheck(load().xlb_batch_step(b, int(n)), b)
+
+
+def xlb_batch_step_per_domain(b, n):
+    _bcheck(load().xlb_batch_step_per_domain(b, int(n)), b)
+
+
+def xlb_batch_set_launch(b, threads, ctas_per_sm):
+    _bcheck(load().xlb_batch_set_launch(b, int(threads), int(ctas_per_sm)), b)
+
+
+def xlb_batch_tune(b, sample_steps, cache_path=None):
+    t, c = C.c_int(), C.c_int()
+    path = cache_path.encode() if cache_path else None
+    _bcheck(load().xlb_batch_tune(b, int(sample_steps), path, C.byref(t), C.byref(c)), b)
+    return t.value, c.value
+
+
+def xlb_batch_macroscopic(b, rho, u):
+    _bcheck(load().xlb_batch_macroscopic(b, _ptr(rho), _ptr(u)), b)
+
+
+def xlb_batch_info(b):
+    n, t, th, ct = C.c_int64(), C.c_int64(), C.c_int(), C.c_int()
+    _bcheck(load().xlb_batch_info(b, C.byref(n), C.byref(t), C.byref(th), C.byref(ct)), b)
+    return {"cells": n.value, "time": t.value, "threads": th.value, "ctas_per_sm": ct.value}
+
+
+def xlb_batch_synchronize(b):
+    _bcheck(load().xlb_batch_synchronize(b), b)
+
+
 # ---- convenience wrapper -------------------------------------------------------
 
 class Simulation:
@@ -369,3 +440,57 @@ class Simulation:
         align = 256 // raw.itemsize
         plane = (self.N + align - 1) // align * align
         return raw.reshape(self.Q, plane)[:, :self.N].reshape((self.Q,) + self.shape), kind_h
+
+
+class Batch:
+    """Many independent D2Q9 domains (dicts with nx, ny, mask[ny, nx] and
+    force (Fx, Fy), as ``inputs.batched_channels`` builds them)."""
+
+    def __init__(self, domains, omega, storage="f32", stream=None):
+        self.domains = domains
+        self.nx = [d["nx"] for d in domains]
+        self.ny = [d["ny"] for d in domains]
+        self.cells = [a * b for a, b in zip(self.nx, self.ny)]
+        self.b = xlb_batch_create(self.nx, self.ny, omega, STORAGE.get(storage, storage), stream)
+
+    def close(self):
+        if self.b:
+            xlb_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_masks(self):
+        masks = np.concatenate([np.ascontiguousarray(d["mask"], np.uint8).reshape(-1) for d in self.domains])
+        forces = np.array([d.get("force", (0.0, 0.0)) for d in self.domains], np.float32).reshape(-1)
+        xlb_batch_set_masks(self.b, masks, forces)
+
+    def init(self, rho=None, u=None):
+        xlb_batch_init(self.b, rho, u)
+
+    def step(self, n):
+        xlb_batch_step(self.b, n)
+
+    def step_per_domain(self, n):
+        xlb_batch_step_per_domain(self.b, n)
+
+    def tune(self, sample_steps=20, cache_path=None):
+        return xlb_batch_tune(self.b, sample_steps, cache_path)
+
+    def macroscopic(self):
+        """Per domain (rho[ny, nx], u[2, ny, nx]) as numpy arrays."""
+        tot = sum(self.cells)
+        rho = np.empty(tot, np.float32)
+        u = np.empty(2 * tot, np.float32)
+        xlb_batch_macroscopic(self.b, rho, u)
+        out, o = [], 0
+        for nx, ny, c in zip(self.nx, self.ny, self.cells):
+            r = rho[o:o + c].reshape(ny, nx)
+            uu = u[2 * o:2 * (o + c)].reshape(ny, nx, 2).transpose(2, 0, 1)
+            out.append((r, uu))
+            o += c
+        return out
