@@ -35,7 +35,7 @@ __device__ __forceinline__ bool cell_of_block(const StepParams& p, CellIdx& c) {
 // Blocks per SM the forward kernels are compiled for (register budget).
 template <int Q, int COLL>
 struct MinBlocks {
-  static constexpr int value = (COLL == 2) ? 4 : (Q == 27 ? 8 : (Q == 19 ? 9 : 12));
+  static constexpr int value = (COLL == 2) ? 5 : (Q == 27 ? 8 : (Q == 19 ? 9 : 12));
 };
 
 // Bulk pass of an update, one thread per cell: pull-stream + collide
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ sr
 
 template <int Q, typename S, int COLL, int V>
 struct VecMinBlocks {
-  static constexpr int value = (COLL == 2) ? 2 : (Q * V > 64 ? 3 : 4);
+  static constexpr int value = (COLL == 2) ? 5 : (Q * V > 64 ? 3 : 4);
 };
 
 template <int Q, typename S, int COLL, int V>

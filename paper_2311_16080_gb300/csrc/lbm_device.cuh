@@ -182,6 +182,21 @@ __device__ __forceinline__ float eq_poly(int i, const float (&u)[3], float usq) 
   return cu * (3.0f + 4.5f * cu) - 1.5f * usq;
 }
 
+// c_i . u
+template <int Q>
+__device__ __forceinline__ float cdot(int i, const float (&u)[3]) {
+  float cu = 0.f;
+  if (Lattice<Q>::c(i, 0)) cu += Lattice<Q>::c(i, 0) * u[0];
+  if (Lattice<Q>::c(i, 1)) cu += Lattice<Q>::c(i, 1) * u[1];
+  if (Lattice<Q>::c(i, 2)) cu += Lattice<Q>::c(i, 2) * u[2];
+  return cu;
+}
+
+// The collision code below walks the rest direction and the pairs
+// (i, opp(i)), i < opp(i): with a = 3 c_i.u and b = 4.5 (c_i.u)^2 - 1.5 u.u
+// the bracket of Eq. 5 is b + a for i and b - a for opp(i), and every even
+// function of c (the KBC shear part, the second moments) is shared.
+
 // Exact-difference body force: df_i += f_i^eq(rho, u + F/rho) - f_i^eq(rho, u).
 template <int Q>
 __device__ __forceinline__ void add_force(float (&df)[Q], float rho, const float (&u)[3], float usq,
@@ -190,8 +205,18 @@ __device__ __forceinline__ void add_force(float (&df)[Q], float rho, const float
   float v[3] = {u[0] + F[0] * ir, u[1] + F[1] * ir, u[2] + F[2] * ir};
   if (Lattice<Q>::D == 2) v[2] = 0.f;
   const float vsq = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const float dsq = -1.5f * (vsq - usq);
+  df[0] += weight<Q>(0) * rho * dsq;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) df[i] += weight<Q>(i) * rho * (eq_poly<Q>(i, v, vsq) - eq_poly<Q>(i, u, usq));
+  for (int i = 1; i < Q; ++i) {
+    if (opposite<Q>(i) > i) {
+      const float cu = cdot<Q>(i, u), cv = cdot<Q>(i, v);
+      const float e = 4.5f * (cv * cv - cu * cu) + dsq, o = 3.0f * (cv - cu);
+      const float wr = weight<Q>(i) * rho;
+      df[i] += wr * (e + o);
+      df[opposite<Q>(i)] += wr * (e - o);
+    }
+  }
 }
 
 // KBC shear population ds_i from hd = D_aa / 2 (a = x, y, z) and
@@ -233,11 +258,19 @@ __device__ __forceinline__ void collide(float (&df)[Q], const StepParams& p) {
     force_u[1] = u[1];
     force_u[2] = u[2];
   }
+  const float b0 = -1.5f * usq;  // b of the rest direction (c = 0)
   if (COLL == COLL_BGK) {
+    df[0] = fmaf(p.omega, weight<Q>(0) * (drho + rho * b0) - df[0], df[0]);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const float dfeq = weight<Q>(i) * (drho + rho * eq_poly<Q>(i, u, usq));
-      df[i] = fmaf(p.omega, dfeq - df[i], df[i]);
+    for (int i = 1; i < Q; ++i) {
+      if (opposite<Q>(i) > i) {
+        const int j = opposite<Q>(i);
+        const float cu = cdot<Q>(i, u);
+        const float bb = drho + rho * fmaf(4.5f * cu, cu, b0), ra = rho * 3.0f * cu;
+        const float w = weight<Q>(i);
+        df[i] = fmaf(p.omega, w * (bb + ra) - df[i], df[i]);
+        df[j] = fmaf(p.omega, w * (bb - ra) - df[j], df[j]);
+      }
     }
   } else {
     // KBC.  Only f^neq stays live; the equilibrium terms and ds are cheap to
@@ -245,40 +278,64 @@ __device__ __forceinline__ void collide(float (&df)[Q], const StepParams& p) {
     //   df_i <- df_i^eq + (1 - beta gamma) f^neq_i - beta (2 - gamma) ds_i.
     float fneq[Q];
     float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx yy zz xy xz yz
+    fneq[0] = df[0] - weight<Q>(0) * (drho + rho * b0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const float fn = df[i] - weight<Q>(i) * (drho + rho * eq_poly<Q>(i, u, usq));
-      fneq[i] = fn;
-      if (Lattice<Q>::c(i, 0)) P[0] += fn;
-      if (Lattice<Q>::c(i, 1)) P[1] += fn;
-      if (Lattice<Q>::c(i, 2)) P[2] += fn;
-      if (Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 1)) P[3] += (float)(Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 1)) * fn;
-      if (Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 2)) P[4] += (float)(Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 2)) * fn;
-      if (Lattice<Q>::c(i, 1) * Lattice<Q>::c(i, 2)) P[5] += (float)(Lattice<Q>::c(i, 1) * Lattice<Q>::c(i, 2)) * fn;
+    for (int i = 1; i < Q; ++i) {
+      if (opposite<Q>(i) > i) {
+        const int j = opposite<Q>(i);
+        const float cu = cdot<Q>(i, u);
+        const float w = weight<Q>(i);
+        const float bb = drho + rho * fmaf(4.5f * cu, cu, b0), ra = rho * 3.0f * cu;
+        const float fi = df[i] - w * (bb + ra), fj = df[j] - w * (bb - ra);
+        fneq[i] = fi;
+        fneq[j] = fj;
+        const float sp = fi + fj;  // second moments are even in c
+        if (Lattice<Q>::c(i, 0)) P[0] += sp;
+        if (Lattice<Q>::c(i, 1)) P[1] += sp;
+        if (Lattice<Q>::c(i, 2)) P[2] += sp;
+        if (Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 1)) P[3] += (float)(Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 1)) * sp;
+        if (Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 2)) P[4] += (float)(Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 2)) * sp;
+        if (Lattice<Q>::c(i, 1) * Lattice<Q>::c(i, 2)) P[5] += (float)(Lattice<Q>::c(i, 1) * Lattice<Q>::c(i, 2)) * sp;
+      }
     }
     constexpr float inv_d = 1.0f / Lattice<Q>::D;
     const float tr = P[0] + P[1] + P[2];
     // ds_i: D_aa / 2 on the axis directions, c_a c_b Pi_ab / 4 on the two-component ones
     const float hd[3] = {0.5f * (P[0] - tr * inv_d), 0.5f * (P[1] - tr * inv_d), 0.5f * (P[2] - tr * inv_d)};
     const float qo[3] = {0.25f * P[3], 0.25f * P[4], 0.25f * P[5]};
-    float sh = 0.f, hh = 0.f;
+    // <a|b> = sum a_i b_i / f_i^eq with f_i^eq = w_i rho (1 + b +- a); the
+    // common 1/rho cancels in gamma.  The rest direction has ds = 0.
+    float hh = fneq[0] * fneq[0] * __fdividef(1.0f / weight<Q>(0), 1.0f + b0), sh = 0.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const float s = kbc_ds<Q>(i, hd, qo);
-      const float dh = fneq[i] - s;
-      // <a|b> weight 1 / f_i^eq, f_i^eq = w_i rho (1 + poly_i); the common 1/rho cancels in gamma
-      const float iw = __fdividef(1.0f / weight<Q>(i), 1.0f + eq_poly<Q>(i, u, usq));
-      sh = fmaf(s * dh, iw, sh);
-      hh = fmaf(dh * dh, iw, hh);
+    for (int i = 1; i < Q; ++i) {
+      if (opposite<Q>(i) > i) {
+        const int j = opposite<Q>(i);
+        const float s_ = kbc_ds<Q>(i, hd, qo);
+        const float cu = cdot<Q>(i, u);
+        const float bq = fmaf(4.5f * cu, cu, b0), a3 = 3.0f * cu;
+        const float iw = 1.0f / weight<Q>(i);
+        const float ri = __fdividef(iw, 1.0f + bq + a3), rj = __fdividef(iw, 1.0f + bq - a3);
+        const float hi = fneq[i] - s_, hj = fneq[j] - s_;
+        sh = fmaf(s_, fmaf(hi, ri, hj * rj), sh);
+        hh = fmaf(hi * hi, ri, fmaf(hj * hj, rj, hh));
+      }
     }
     const float beta = 0.5f * p.omega;
     const float ib = 1.0f / beta;
     const float gamma = (hh < 1e-20f * rho) ? 2.0f : ib - (2.0f - ib) * sh / hh;
     const float a1 = 1.0f - beta * gamma, a2 = beta * (2.0f - gamma);
+    df[0] = weight<Q>(0) * (drho + rho * b0) + a1 * fneq[0];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const float dfeq = weight<Q>(i) * (drho + rho * eq_poly<Q>(i, u, usq));
-      df[i] = dfeq + a1 * fneq[i] - a2 * kbc_ds<Q>(i, hd, qo);
+    for (int i = 1; i < Q; ++i) {
+      if (opposite<Q>(i) > i) {
+        const int j = opposite<Q>(i);
+        const float cu = cdot<Q>(i, u);
+        const float w = weight<Q>(i);
+        const float bb = drho + rho * fmaf(4.5f * cu, cu, b0), ra = rho * 3.0f * cu;
+        const float sd = a2 * kbc_ds<Q>(i, hd, qo);
+        df[i] = w * (bb + ra) + a1 * fneq[i] - sd;
+        df[j] = w * (bb - ra) + a1 * fneq[j] - sd;
+      }
     }
   }
   if (p.has_force) add_force<Q>(df, rho, force_u, usq, p.F);
