@@ -106,6 +106,22 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """Slowest rank's time (the whole job ends when the slowest replica ends)."""
+    if not dist:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(cells_per_rank, steps, world, ms_max):
+    """Whole-job throughput of N independent replicas: all ranks' updates over
+    the slowest rank's time (weak scaling)."""
+    return world * cells_per_rank * steps / (ms_max * 1e3)
+
+
 # ---------------------------------------------------------------------------
 # our arm
 
@@ -157,15 +173,10 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     mass, _ = sim.reduce()  # FP64 conservation check on every benchmark run
     ms_step = ms_max / args.steps
-    mlups = world * cells * args.steps / (ms_max * 1e3)
+    mlups = job_mlups(cells, args.steps, world, ms_max)
 
     # end to end through the public API with host buffers: upload mask and
     # initial fields from pinned memory, K steps, read rho and u back.

@@ -33,9 +33,13 @@ __device__ __forceinline__ bool cell_of_block(const StepParams& p, CellIdx& c) {
 }
 
 // Blocks per SM the forward kernels are compiled for (register budget).
-template <int Q, int COLL>
+#ifndef XLB_MINB_Q19_16
+#define XLB_MINB_Q19_16 9
+#endif
+template <int Q, typename S, int COLL>
 struct MinBlocks {
-  static constexpr int value = (COLL == 2) ? 5 : (Q == 27 ? 8 : (Q == 19 ? 9 : 12));
+  static constexpr int value =
+      (COLL == 2) ? 5 : (Q == 27 ? 8 : (Q == 19 ? (sizeof(S) == 2 ? XLB_MINB_Q19_16 : 9) : 12));
 };
 
 // Bulk pass of an update, one thread per cell: pull-stream + collide
@@ -45,7 +49,7 @@ struct MinBlocks {
 // cells get values nobody reads until k_boundary rewrites them; inlet /
 // outlet cells are recomputed there too.
 template <int Q, typename S, int COLL>
-__global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, COLL>::value)
+__global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, S, COLL>::value)
     k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, const StepParams p) {
   CellIdx c;
   if (!cell_of_block(p, c)) return;
