@@ -47,7 +47,11 @@ Readings of points the paper leaves open (each also listed in the design doc):
   definition checks this rule;
 * observables are those of the post-stream state f_t; the reported velocity
   with a body force is (j + F/2) / rho;
-* solid (WALL, LID) cells report rho = 0, u = 0.
+* solid (WALL, LID) cells report rho = 0, u = 0;
+* FWALL cells are full-way bounce-back walls (the walls of the paper's
+  performance setup, Section 5): they are streamed like any cell, their
+  collision reverses every population (f*_i = f_opp(i)), they start at rest
+  and report rho = 0, u = 0.
 """
 from __future__ import annotations
 
@@ -58,7 +62,7 @@ import numpy as np
 # ---------------------------------------------------------------------------
 # Cell types of the per-cell mask (Section 3.5).  The numeric codes are the
 # library's public ABI values; the oracle keeps its own copy.
-FLUID, WALL, LID, INLET, OUTLET, EQ = 0, 1, 2, 3, 4, 5
+FLUID, WALL, LID, INLET, OUTLET, EQ, FWALL = 0, 1, 2, 3, 4, 5, 6
 FLUID_LIKE = (FLUID, INLET, OUTLET)
 
 CS2 = 1.0 / 3.0  # speed of sound squared, Section 2 (after Eq. 4)
@@ -363,7 +367,8 @@ class Params:
 
 
 def collide(lat: Lattice, f, mask, p: Params):
-    """C: collision (+ body force) on fluid-like cells, identity elsewhere."""
+    """C: collision (+ body force) on fluid-like cells; FWALL cells reverse
+    their populations (full-way bounce-back); identity elsewhere."""
     if p.collision == "none":
         return f
     if p.collision == "bgk":
@@ -375,7 +380,11 @@ def collide(lat: Lattice, f, mask, p: Params):
     if p.force is not None:
         h = h + force_increment(lat, f, p.force)
     fl = fluid_like(mask)
-    return np.where(fl[None], h, f)
+    out = np.where(fl[None], h, f)
+    fw = mask == FWALL
+    if fw.any():
+        out = np.where(fw[None], f[lat.opp], out)
+    return out
 
 
 def step(lat: Lattice, f, mask, p: Params):
@@ -394,7 +403,7 @@ def init_state(lat: Lattice, rho, u, mask, p: Params):
     fixed values of the mask types."""
     f = equilibrium(lat, rho, u)
     feq_w = _const_feq(lat, p.bc.eq_rho, p.bc.eq_u)
-    solid = (mask == WALL) | (mask == LID)
+    solid = (mask == WALL) | (mask == LID) | (mask == FWALL)
     for i in range(lat.q):
         f[i] = np.where(mask == EQ, feq_w[i], f[i])
         f[i] = np.where(solid, lat.w[i], f[i])
@@ -410,7 +419,7 @@ def macroscopic(lat: Lattice, f, mask, p: Params):
         fl = fluid_like(mask)
         j = np.stack([j[a] + np.where(fl, 0.5 * p.force[a], 0.0) for a in range(lat.d)])
     u = j / rho
-    solid = (mask == WALL) | (mask == LID)
+    solid = (mask == WALL) | (mask == LID) | (mask == FWALL)
     rho = np.where(solid, 0.0, rho)
     u = np.where(solid[None], 0.0, u)
     return rho, u
@@ -462,8 +471,8 @@ def stream_bc_vjp(lat: Lattice, fbar, mask, bc: BC):
     A population f_i(x) at a fluid-like cell x depends on h_i(x - c_i) when the
     source is fluid-like, on h_opp(i)(x) for a WALL or LID source, and on no
     h for an EQ source."""
-    if np.isin(mask, (INLET, OUTLET)).any():
-        raise ValueError("adjoint of the inlet/outlet rules is not defined")
+    if np.isin(mask, (INLET, OUTLET, FWALL)).any():
+        raise ValueError("adjoint of the inlet/outlet and full-way rules is not defined")
     fl = fluid_like(mask)
     hbar = np.zeros_like(fbar)
     for i in range(lat.q):

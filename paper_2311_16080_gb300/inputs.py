@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import numpy as np
 
-FLUID, WALL, LID, INLET, OUTLET, EQ = 0, 1, 2, 3, 4, 5
+FLUID, WALL, LID, INLET, OUTLET, EQ, FWALL = 0, 1, 2, 3, 4, 5, 6
 
 
 def taylor_green_2d(nx, ny, u0=0.04, rho0=1.0):
@@ -54,6 +54,16 @@ def lid_driven_cavity_mask(n, ny=None, nz=None):
     m[:, ny - 1, :] = WALL
     m[:, :, 0] = WALL
     m[:, :, nx - 1] = WALL
+    return m
+
+
+def paper_cavity_mask(n, ny=None, nz=None):
+    """The cavity of the paper's performance runs (Section 5): full-way
+    bounce-back walls (FWALL) on five faces and an equilibrium-BC lid (EQ) on
+    the top plane z = nz-1, whose edges shared with a wall are FWALL."""
+    m = lid_driven_cavity_mask(n, ny, nz)
+    m[m == WALL] = FWALL
+    m[m == LID] = EQ
     return m
 
 

@@ -142,11 +142,12 @@ def test_stream_only_is_a_permutation_bruteforce():
 
 
 def test_pull_rules_bruteforce():
-    """WALL / LID / EQ substitution of the pull, against per-cell loops."""
+    """WALL / LID / EQ substitution of the pull (FWALL sources pulled
+    plainly), against per-cell loops."""
     lat = O.Lattice(9)
     ny, nx = 5, 6
     rng = np.random.default_rng(11)
-    mask = rng.choice([O.FLUID, O.FLUID, O.FLUID, O.WALL, O.LID, O.EQ], size=(ny, nx)).astype(np.uint8)
+    mask = rng.choice([O.FLUID, O.FLUID, O.FLUID, O.WALL, O.LID, O.EQ, O.FWALL], size=(ny, nx)).astype(np.uint8)
     h = rng.standard_normal((9, ny, nx))
     bc = O.BC(2, lid_u=(0.03, -0.02), lid_rho=1.0, eq_rho=1.01, eq_u=(0.01, 0.02))
     f = O.pull_plain(lat, h, mask, bc)
@@ -167,6 +168,94 @@ def test_pull_rules_bruteforce():
                 else:
                     ref = h[i, (y - cy) % ny, (x - cx) % nx]
                 assert abs(f[i, y, x] - ref) <= 1e-15 * max(1.0, abs(ref))
+
+
+def test_fullway_collision_reverses_bruteforce():
+    """Full-way bounce-back (Section 3.5): the collision of an FWALL cell
+    returns every population in the opposite direction, f*_i = f_opp(i), per
+    cell loops on a random D3Q19 state; other non-fluid cells keep their
+    populations, and with no collision FWALL cells are left alone too."""
+    lat = O.Lattice(19)
+    rng = np.random.default_rng(12)
+    shape = (3, 4, 5)
+    mask = rng.choice([O.FLUID, O.FWALL, O.FWALL, O.WALL, O.EQ], size=shape).astype(np.uint8)
+    f = lat.w[:, None, None, None] * (1.0 + 0.1 * rng.standard_normal((19,) + shape))
+    h = O.collide(lat, f, mask, O.Params(lat, 1.3))
+    for z, y, x in itertools.product(*(range(n) for n in shape)):
+        for i in range(19):
+            if mask[z, y, x] == O.FWALL:
+                assert h[i, z, y, x] == f[int(lat.opp[i]), z, y, x]
+            elif mask[z, y, x] != O.FLUID:
+                assert h[i, z, y, x] == f[i, z, y, x]
+    g = O.collide(lat, f, mask, O.Params(lat, 1.3, collision="none"))
+    assert np.array_equal(g, f)
+
+
+def test_fullway_poiseuille_exact_at_magic_tau():
+    """Force-driven channel between full-way bounce-back walls, BGK with
+    tau = 1/2 + sqrt(3/16): the steady lattice solution is the parabola with
+    the no-slip planes half a cell outside the first fluid rows, as for the
+    halfway walls (the wall cells hold the reversed populations one step)."""
+    lat = O.Lattice(9)
+    H = 8
+    omega = 1.0 / (0.5 + np.sqrt(3.0 / 16.0))
+    F = 1e-5
+    nu = O.nu_from_omega(omega)
+    mask = I.channel_2d_mask(4, H + 2, top=O.FWALL, bottom=O.FWALL)
+    p = O.Params(lat, omega, force=(F, 0.0))
+    y = np.arange(H)
+    ref = F / (2 * nu) * (y + 0.5) * (H - 0.5 - y)
+    rho = np.ones(mask.shape)
+    u = np.zeros((2,) + mask.shape)
+    u[0, 1:H + 1, :] = ref[:, None]
+    f = O.run(lat, O.init_state(lat, rho, u, mask, p), mask, p, 3000)
+    _, uu = O.macroscopic(lat, f, mask, p)
+    assert np.max(np.abs(uu[0, 1:H + 1, 2] - ref)) < 1e-10 * ref.max()
+    assert np.all(uu[:, mask == O.FWALL] == 0.0)
+
+
+def test_fullway_box_conserves_mass():
+    """A closed box of FWALL walls with FWALL and WALL obstacles: the mass of
+    the fluid cells plus the populations in transit through FWALL cells is
+    constant (BGK conserves it per cell, the reversal and the plain pull
+    permute, halfway walls return what they receive)."""
+    lat = O.Lattice(19)
+    mask = I.lid_driven_cavity_mask(8)
+    mask[mask != O.FLUID] = O.FWALL
+    mask[I.random_obstacle_mask(mask.shape, 0.04, seed=3) == O.WALL] = O.WALL
+    mask[I.random_obstacle_mask(mask.shape, 0.04, seed=4) == O.WALL] = O.FWALL
+    p = O.Params(lat, 1.5)
+    f = _perturbed_state(lat, mask.shape, seed=6)
+    f = O.init_state(lat, O.density(lat, f), O.momentum(lat, f) / O.density(lat, f), mask, p)
+    held = (mask == O.FLUID) | (mask == O.FWALL)
+
+    def mass(g):
+        return float(O.density(lat, g)[held].sum())
+
+    m0 = mass(f)
+    f = O.run(lat, f, mask, p, 200)
+    assert abs(mass(f) - m0) < 1e-12 * m0
+
+
+def test_paper_cavity_mirror_symmetry():
+    """The performance cavity of Section 5 (FWALL walls, EQ lid moving along
+    x) is symmetric under y -> ny - 1 - y: from a symmetric start the flow
+    stays mirror-symmetric with u_y odd, to rounding.  A wrong direction
+    index, a transposed axis or a misplaced lid breaks it."""
+    lat = O.Lattice(19)
+    n = 10
+    mask = I.paper_cavity_mask(n)
+    assert mask[n - 1, n // 2, n // 2] == O.EQ and mask[n - 1, 0, n // 2] == O.FWALL
+    p = O.Params(lat, 1.2, bc=O.BC(3, eq_rho=1.0, eq_u=(0.05, 0.0, 0.0)))
+    rho = np.ones(mask.shape)
+    u = np.zeros((3,) + mask.shape)
+    f = O.run(lat, O.init_state(lat, rho, u, mask, p), mask, p, 60)
+    r, uu = O.macroscopic(lat, f, mask, p)
+    assert np.abs(uu[0]).max() > 1e-3
+    np.testing.assert_allclose(r, r[:, ::-1, :], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(uu[0], uu[0][:, ::-1, :], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(uu[1], -uu[1][:, ::-1, :], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(uu[2], uu[2][:, ::-1, :], rtol=0, atol=1e-13)
 
 
 def test_kbc_gamma_two_is_bgk():
