@@ -273,6 +273,22 @@ def extras(args, torch, X, I, stream):
         res[f"cavity256_{st}_algo_GBs"] = round(2 * 19 * 2 * n ** 3 / (ms * 1e-3) / 1e9, 1)
         sim.close()
 
+    # the paper's own performance cavity (Section 5): full-way bounce-back
+    # walls and an equilibrium-BC lid, same lattice, size and viscosity
+    pmask = I.paper_cavity_mask(n)
+    for st in ("f32", "f16"):
+        sim = X.Simulation(19, (n, n, n), cavity_omega(n), "bgk", st, stream=stream.cuda_stream)
+        sim.set_mask(pmask)
+        sim.set_bc(X.XLB_CELL_EQ, 1.0, (LID_U, 0.0, 0.0))
+        sim.init()
+        sim.step(10)
+        ms = timed(sim, 300)
+        esz = 4 if st == "f32" else 2
+        res[f"paper_cavity256_fullway_eq_lid_{st}_mlups"] = round(n ** 3 / (ms * 1e3), 1)
+        res[f"paper_cavity256_fullway_eq_lid_{st}_algo_GBs"] = round(2 * 19 * esz * n ** 3 / (ms * 1e-3) / 1e9, 1)
+        sim.close()
+    del pmask
+
     # KBC D3Q27 flow past a sphere, 512 x 256 x 256, Zou-He inlet + outflow
     mask = I.sphere_channel_mask(512, 256, 256, radius=32, center=(128, 128, 128))
     for st in ("f32", "f16"):

@@ -55,22 +55,27 @@ enum { XLB_COLL_NONE = 0, XLB_COLL_BGK = 1, XLB_COLL_KBC = 2 };
  * f_i - w_i rounded to nearest even (the centring Section 4.1 cites). */
 enum { XLB_STORE_F32 = 0, XLB_STORE_F16 = 1, XLB_STORE_BF16 = 2 };
 
-/* Cell types of the mask (Section 3.5).  For a fluid-like cell x and a
- * direction i whose source cell x - c_i is
- *   FLUID/INLET/OUTLET: f_i(x) = h_i(x - c_i)                 (Eq. 2, periodic)
+/* Cell types of the mask (Section 3.5).  For a fluid-like or FWALL cell x
+ * and a direction i whose source cell x - c_i is
+ *   FLUID/INLET/OUTLET/FWALL: f_i(x) = h_i(x - c_i)           (Eq. 2, periodic)
  *   WALL:   f_i(x) = h_opp(i)(x)                                (halfway bounce-back)
  *   LID:    f_i(x) = h_opp(i)(x) + 2 w_i rho_w (c_i . u_w) / cs^2 (moving wall)
  *   EQ:     f_i(x) = f_i^eq(rho_w, u_w)                         (equilibrium BC)
  * where h is the post-collision state.  INLET cells then rebuild their c_x=+1
  * populations by Zou-He for the inlet velocity; OUTLET cells copy their
- * c_x=-1 populations from the cell at x-1 (zero-gradient outflow). */
+ * c_x=-1 populations from the cell at x-1 (zero-gradient outflow).  FWALL
+ * cells are full-way bounce-back walls (the walls of the Section 5 cavity):
+ * they stream like fluid cells, their collision is h_i = f_opp(i) (none under
+ * XLB_COLL_NONE), they start at rest and report rho = 0, u = 0; the mass
+ * they hold in transit is outside the fluid-cell sums of xlb_reduce. */
 enum {
   XLB_CELL_FLUID = 0,
   XLB_CELL_WALL = 1,
   XLB_CELL_LID = 2,
   XLB_CELL_INLET = 3,
   XLB_CELL_OUTLET = 4,
-  XLB_CELL_EQ = 5
+  XLB_CELL_EQ = 5,
+  XLB_CELL_FWALL = 6
 };
 
 /* ---- simulation context ------------------------------------------------ */
@@ -100,18 +105,21 @@ const char* xlb_status_string(int status);
 double xlb_omega_from_nu(double nu);
 
 /* Set the per-cell type mask (uint8 codes XLB_CELL_*, N cells, x fastest).
- * Codes >= 6 give XLB_ERR_ARG and leave the previous mask in place.  Between
+ * Codes >= 7 give XLB_ERR_ARG and leave the previous mask in place.  Between
  * steps, a new mask (like new boundary values from xlb_set_bc) acts from the
  * next step on: the current state keeps the boundaries it was streamed with.
  * XLB_ERR_STATE while a tape is open. */
 int xlb_set_mask(xlb_ctx* ctx, const uint8_t* mask);
 
-/* Sizes of the boundary tables of the current mask: n_links = number of
- * (fluid cell, direction) pairs whose source cell is WALL, LID or EQ; n_fix
- * = number of INLET and OUTLET cells.  After each update a boundary pass
+/* Sizes of the boundary tables of the current mask.  Whole face planes that
+ * the mask fills with one boundary type are handled by coordinates and need
+ * no table.  n_links = number of (cell, direction) pairs, over FLUID cells
+ * and FWALL cells of FWALL face planes, whose source cell is WALL, LID or EQ
+ * off the face planes; n_fix = number of INLET and OUTLET cells plus the
+ * FWALL cells off the face planes.  After each update a boundary pass
  * writes, for every link, the value the rule prescribes into the source
  * cell's slot for that direction (a ghost value, so the next update can pull
- * every cell as if periodic) and recomputes the inlet / outlet cells. */
+ * every cell as if periodic) and recomputes the fix-up cells. */
 int xlb_boundary_links(const xlb_ctx* ctx, int64_t* n_links, int64_t* n_fix);
 
 /* Prescribed state of a boundary type: XLB_CELL_LID (rho_w, u_w of the
@@ -198,7 +206,7 @@ int xlb_populations(xlb_ctx* ctx, void** dev_ptr, int64_t* plane_stride);
 /* Open a tape right after xlb_init: the next xlb_step calls (n_steps in
  * total) record a checkpoint every checkpoint_every steps.  The adjoint then
  * recomputes each segment from its checkpoint.  BGK or NONE collision; masks
- * with INLET / OUTLET cells are XLB_ERR_UNSUPPORTED. */
+ * with INLET / OUTLET / FWALL cells are XLB_ERR_UNSUPPORTED. */
 int xlb_tape_begin(xlb_ctx* ctx, int64_t n_steps, int64_t checkpoint_every);
 
 /* Seed the adjoint at the final step with the loss cotangents of the
@@ -232,7 +240,8 @@ int xlb_tape_release(xlb_ctx* ctx);
  *     (16-bit storage, D2Q9 / D3Q19, BGK / NONE, nx % 4 == 0);
  *   XLB_KERNEL_AUTO:   VEC where possible on lattices without boundary faces
  *     (whole face planes the mask fills with one boundary type), else DIRECT
- *     (the default). */
+ *     (the default).
+ * A mask with an FWALL face plane always runs DIRECT. */
 enum { XLB_KERNEL_AUTO = 0, XLB_KERNEL_DIRECT = 1, XLB_KERNEL_VEC = 2 };
 
 /* Choose the variant (XLB_ERR_UNSUPPORTED if it cannot run this ctx). */

@@ -47,7 +47,7 @@ struct xlb_ctx {
   int* fix = nullptr;  // inlet / outlet cells (recomputed after a bulk pass)
   long long n_fix = 0;
   int face[6] = {0, 0, 0, 0, 0, 0};  // described boundary faces (StepParams::face)
-  bool has_inlet_outlet = false;
+  bool has_inlet_outlet = false;  // INLET, OUTLET or FWALL cells (no adjoint)
   float* init_fields = nullptr;  // (1 + D) * N: rho0, u0 (component-major)
   bool has_init = false;
   int kind_h = 0;
@@ -234,11 +234,18 @@ static bool vec_possible(const xlb_ctx* c) {
   return c->esize == 2 && c->Q != 27 && c->coll != XLB_COLL_KBC && c->nx % 4 == 0;
 }
 
+// The vectorised kernel has no full-way reversal for FWALL face planes.
+static bool has_fwall_face(const xlb_ctx* c) {
+  for (int f = 0; f < 6; ++f)
+    if (c->face[f] == XLB_CELL_FWALL) return true;
+  return false;
+}
+
 // AUTO takes VEC only on lattices without boundary faces: with faces, every
 // warp of a 4-cell-per-thread row holds a face-adjacent lane (measured slower
 // than one cell per thread on the 256^3 cavity).
 static bool use_vec(const xlb_ctx* c) {
-  if (c->variant == XLB_KERNEL_DIRECT || !vec_possible(c)) return false;
+  if (c->variant == XLB_KERNEL_DIRECT || !vec_possible(c) || has_fwall_face(c)) return false;
   if (c->variant == XLB_KERNEL_VEC) return true;
   for (int f = 0; f < 6; ++f)
     if (c->face[f]) return false;
@@ -326,8 +333,9 @@ static int launch_init(xlb_ctx* c, void* dst) {
 // Boundary faces of a mask (host copy): a face plane qualifies when none of
 // its cells is fluid-like; its type is that of the plane's centre cell.  A
 // face stays only while every cell of its plane has the type the pull derives
-// from the remaining faces (WALL wins where planes meet; at most one other
-// type among LID / EQ); dropped faces are covered by ghost links.
+// from the remaining faces (where planes meet WALL wins, then FWALL; at most
+// one other type among LID / EQ); dropped faces are covered by ghost links
+// and the fix-up list.  Axes of extent 1 carry no faces.
 static void detect_faces(const uint8_t* m, long long nx, long long ny, long long nz, int out[6]) {
   for (int f = 0; f < 6; ++f) out[f] = 0;
   const long long ext[3] = {nx, ny, nz};
@@ -336,7 +344,7 @@ static void detect_faces(const uint8_t* m, long long nx, long long ny, long long
   int cand[6] = {0, 0, 0, 0, 0, 0};
   for (int f = 0; f < 6; ++f) {
     const int ax = f / 2;
-    if (ax == 2 && nz == 1) continue;
+    if (ext[ax] < 2) continue;
     const long long pos = (f % 2) ? ext[ax] - 1 : 0;
     const long long n1 = ext[(ax + 1) % 3], n2 = ext[(ax + 2) % 3];
     bool ok = true;
@@ -354,11 +362,11 @@ static void detect_faces(const uint8_t* m, long long nx, long long ny, long long
     q[(ax + 1) % 3] = n1 / 2;
     q[(ax + 2) % 3] = n2 / 2;
     const int t = at(q[0], q[1], q[2]);
-    if (t == XLB_CELL_WALL || t == XLB_CELL_LID || t == XLB_CELL_EQ) cand[f] = t;
+    if (t == XLB_CELL_WALL || t == XLB_CELL_LID || t == XLB_CELL_EQ || t == XLB_CELL_FWALL) cand[f] = t;
   }
   int other = 0;
   for (int f = 0; f < 6; ++f)
-    if (cand[f] && cand[f] != XLB_CELL_WALL) {
+    if (cand[f] == XLB_CELL_LID || cand[f] == XLB_CELL_EQ) {
       if (other && other != cand[f]) return;
       other = cand[f];
     }
@@ -378,7 +386,7 @@ static void detect_faces(const uint8_t* m, long long nx, long long ny, long long
           q[ax] = pos;
           q[(ax + 1) % 3] = a;
           q[(ax + 2) % 3] = b;
-          int tw = 0, to = 0;
+          int tw = 0, tf = 0, to = 0;
           for (int g = 0; g < 6; ++g) {
             if (!cand[g]) continue;
             const int gx = g / 2;
@@ -386,11 +394,13 @@ static void detect_faces(const uint8_t* m, long long nx, long long ny, long long
             if (q[gx] == gp) {
               if (cand[g] == XLB_CELL_WALL)
                 tw = XLB_CELL_WALL;
+              else if (cand[g] == XLB_CELL_FWALL)
+                tf = XLB_CELL_FWALL;
               else
                 to = cand[g];
             }
           }
-          bad = at(q[0], q[1], q[2]) != (tw ? tw : to);
+          bad = at(q[0], q[1], q[2]) != (tw ? tw : (tf ? tf : to));
         }
       if (bad) {
         cand[f] = 0;
@@ -540,9 +550,9 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
   CK(cudaStreamSynchronize(c->stream));
   if (herr) {
     cudaFree(nf);
-    return fail(c, XLB_ERR_ARG, "mask holds a code >= 6");
+    return fail(c, XLB_ERR_ARG, "mask holds a code >= 7");
   }
-  // does the mask hold inlet / outlet cells (adjoint support check)?
+  // does the mask hold inlet / outlet / FWALL cells (adjoint support check)?
   {
     std::vector<uint8_t> h;
     const uint8_t* hp = mask;
@@ -552,7 +562,8 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
       hp = h.data();
     }
     bool io = false;
-    for (size_t k = 0; k < n && !io; ++k) io = (hp[k] == XLB_CELL_INLET || hp[k] == XLB_CELL_OUTLET);
+    for (size_t k = 0; k < n && !io; ++k)
+      io = (hp[k] == XLB_CELL_INLET || hp[k] == XLB_CELL_OUTLET || hp[k] == XLB_CELL_FWALL);
     new_io = io;
     detect_faces(hp, c->nx, c->ny, c->nz, new_face);
   }
@@ -904,7 +915,8 @@ int xlb_tape_begin(xlb_ctx* c, int64_t n_steps, int64_t k) {
   if (n_steps < 1 || k < 1) return fail(c, XLB_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
   if (c->t != 0 || c->kind_h || !c->has_init) return fail(c, XLB_ERR_STATE, "open a tape right after xlb_init");
   if (c->coll == XLB_COLL_KBC) return fail(c, XLB_ERR_UNSUPPORTED, "the adjoint covers BGK and NONE collisions");
-  if (c->has_inlet_outlet) return fail(c, XLB_ERR_UNSUPPORTED, "the adjoint does not cover inlet/outlet cells");
+  if (c->has_inlet_outlet)
+    return fail(c, XLB_ERR_UNSUPPORTED, "the adjoint does not cover inlet/outlet or full-way (FWALL) cells");
   xlb_tape_end(c);
   if (k > n_steps) k = n_steps;
   const int64_t n_ckpt = (n_steps - 1) / k;

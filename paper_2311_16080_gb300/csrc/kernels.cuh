@@ -48,7 +48,10 @@ struct MinBlocks {
 // exact for every fluid cell; dst receives h_t = C(S_bc(h_{t-1})).  Boundary
 // cells get values nobody reads until k_boundary rewrites them; inlet /
 // outlet cells are recomputed there too.
-template <int Q, typename S, int COLL>
+// FW: the lattice has FWALL face planes (their cells reverse instead of
+// colliding, and pulls from them are plain); the FW = false instance carries
+// none of that logic.
+template <int Q, typename S, int COLL, bool FW>
 __global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, S, COLL>::value)
     k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, const StepParams p) {
   CellIdx c;
@@ -56,8 +59,11 @@ __global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, S, COLL>::value)
   Nbr nb;
   make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
   float df[Q];
-  pull_periodic<Q, S>(src, p, nb, c.self, c.x, c.y, c.z, df);
-  collide<Q, COLL>(df, p);
+  pull_periodic<Q, S, FW>(src, p, nb, c.self, c.x, c.y, c.z, df);
+  if (FW && COLL != COLL_NONE && on_fwall_face(p, c.x, c.y, c.z))
+    reverse_populations<Q>(df);
+  else
+    collide<Q, COLL>(df, p);
   S* out = dst + c.self;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -95,10 +101,10 @@ __device__ __forceinline__ void write_ghost(S* __restrict__ dst, const StepParam
 
 // Boundary pass on dst, after a pass that wrote post-collision values there.
 // Threads [0, ceil(n_links / 4)) write the ghost values of the links of FLUID
-// cells (4 links each); the next n_fix threads handle one INLET or
-// OUTLET cell each: with `recompute`, its update from src with the full
-// rules (the bulk pass pulled it as if periodic); then the ghosts of its own
-// links.  src is read only by the recomputation, which needs the ghosts of
+// cells and of cells on FWALL face planes (4 links each); the next n_fix
+// threads handle one INLET, OUTLET or other FWALL cell each: with
+// `recompute`, its update from src with the full rules (the bulk pass pulled
+// and collided it as if periodic fluid); then the ghosts of its own links.  src is read only by the recomputation, which needs the ghosts of
 // the previous state, already in src.
 constexpr int LINKS_PER_THREAD = 4;
 
@@ -149,8 +155,13 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ sr
   make_nbr(nb, x, y, z, p.nx, p.ny, p.nz);
   float df[Q];
   if (recompute) {
-    pull_cell<Q, S>(src, p, x, y, z, __ldg(p.flags + self) & FLAG_TYPE, nb, df);
-    collide<Q, COLL>(df, p);
+    const int type = __ldg(p.flags + self) & FLAG_TYPE;
+    pull_cell<Q, S>(src, p, x, y, z, type, nb, df);
+    if (type == FWALL) {
+      if (COLL != COLL_NONE) reverse_populations<Q>(df);
+    } else {
+      collide<Q, COLL>(df, p);
+    }
     S* out = dst + self;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -164,7 +175,7 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ sr
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const int t = __ldg(p.flags + src_index<Q>(nb, i)) & FLAG_TYPE;
-    if (!fluid_like(t)) {
+    if (!holds_state(t)) {
       // the stored (rounded) value, as the link threads read it
       S hs;
       Store<S>::st(&hs, df[opposite<Q>(i)]);
@@ -266,7 +277,7 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
       const S* own = src + (long long)opposite<Q>(i) * p.plane + self0;
 #pragma unroll
       for (int k = 0; k < V; ++k) {
-        const int t = face_combine(tx[k][1 - cx], ty[1 - Lattice<Q>::c(i, 1)], tz[1 - Lattice<Q>::c(i, 2)]);
+        const int t = face_combine<false>(tx[k][1 - cx], ty[1 - Lattice<Q>::c(i, 1)], tz[1 - Lattice<Q>::c(i, 2)]);
         if (t == WALL || t == LID) v[i][k] = Store<S>::ld(own + k);
       }
     }
@@ -277,8 +288,8 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
     for (int i = 1; i < Q; ++i)
 #pragma unroll
       for (int k = 0; k < V; ++k) {
-        const int t = face_combine(tx[k][1 - Lattice<Q>::c(i, 0)], ty[1 - Lattice<Q>::c(i, 1)],
-                                   tz[1 - Lattice<Q>::c(i, 2)]);
+        const int t = face_combine<false>(tx[k][1 - Lattice<Q>::c(i, 0)], ty[1 - Lattice<Q>::c(i, 1)],
+                                          tz[1 - Lattice<Q>::c(i, 2)]);
         if (t == EQ) v[i][k] = p.eq_df[i];
         if (t == LID) v[i][k] += p.lid_term[i];
       }
@@ -307,11 +318,15 @@ template <int Q, typename S, int COLL>
 __global__ void __launch_bounds__(ROW_BLOCK) k_collide_local(S* f, const StepParams p) {
   CellIdx c;
   if (!cell_of_block(p, c)) return;
-  if (p.has_mask && !fluid_like(p.flags[c.self] & FLAG_TYPE)) return;
+  const int t = p.has_mask ? (p.flags[c.self] & FLAG_TYPE) : FLUID;
+  if (!holds_state(t) || (t == FWALL && COLL == COLL_NONE)) return;
   float df[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) df[i] = Store<S>::ld_plain(f + (long long)i * p.plane + c.self);
-  collide<Q, COLL>(df, p);
+  if (t == FWALL)
+    reverse_populations<Q>(df);
+  else
+    collide<Q, COLL>(df, p);
 #pragma unroll
   for (int i = 0; i < Q; ++i) Store<S>::st(f + (long long)i * p.plane + c.self, df[i]);
 }
@@ -469,7 +484,11 @@ int launch_typed(Op op, const LaunchArgs& a) {
   cudaStream_t st = (cudaStream_t)a.stream;
   switch (op) {
     case OP_STEP:
-      k_stream_collide<Q, S, COLL><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, p);
+      if (p.face[0] == FWALL || p.face[1] == FWALL || p.face[2] == FWALL || p.face[3] == FWALL ||
+          p.face[4] == FWALL || p.face[5] == FWALL)
+        k_stream_collide<Q, S, COLL, true><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, p);
+      else
+        k_stream_collide<Q, S, COLL, false><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, p);
       return 0;
     case OP_STEP_VEC: {
       // 16-bit storage, BGK / NONE, D2Q9 / D3Q19 only (FP32 is faster with one

@@ -47,8 +47,8 @@ __device__ __forceinline__ int src_index(const Nbr& nb, int i) {
 // (StepParams::face) take the rule instead, chosen before any load so that
 // each direction is still exactly one load:
 //   WALL: h_opp(i)(x);  LID: h_opp(i)(x) + 2 w_i rho_w (c_i . u_w) / cs^2;
-//   EQ: f_i^eq(rho_w, u_w) (no load).
-// Sources elsewhere that are not fluid hold ghost values (k_boundary).
+//   EQ: f_i^eq(rho_w, u_w) (no load);  FWALL: the plain pull.
+// WALL / LID / EQ sources elsewhere hold ghost values (k_boundary).
 
 // Face type of the source coordinate index k (0: v - 1, 1: v, 2: v + 1) on
 // one axis: lo / hi are the face types of coordinate 0 and n - 1.
@@ -56,13 +56,41 @@ __device__ __forceinline__ int face_code(int v, int n) {
   return (v == 0 ? 1 : 0) | (v == n - 1 ? 2 : 0);
 }
 
-// Source type from the three axes' face types: WALL wins, else LID / EQ.
+// Rule a source takes, from the three axes' face types of its coordinates:
+// WALL wins; then a source on an FWALL plane is pulled plainly (0); else LID
+// / EQ (at most one of the two meets; verified on the host).  FW = false
+// compiles the form for lattices without FWALL faces.
+template <bool FW = true>
 __device__ __forceinline__ int face_combine(int a, int b, int c) {
   if (a == WALL || b == WALL || c == WALL) return WALL;
-  return a | b | c;  // at most one non-wall type meets (verified on the host)
+  if (FW && (a == FWALL || b == FWALL || c == FWALL)) return 0;
+  return a | b | c;
 }
 
-template <int Q, typename S>
+// Does cell (x, y, z) lie on an FWALL face plane?
+// Such a cell reverses its populations instead of colliding.  Where a WALL
+// face meets the plane the cell is WALL and its slots are never read, so
+// reversing it there too is harmless.
+__device__ __forceinline__ bool on_fwall_face(const StepParams& p, int x, int y, int z) {
+  return (p.face[0] == FWALL && x == 0) || (p.face[1] == FWALL && x == p.nx - 1) ||
+         (p.face[2] == FWALL && y == 0) || (p.face[3] == FWALL && y == p.ny - 1) ||
+         (p.face[4] == FWALL && z == 0) || (p.face[5] == FWALL && z == p.nz - 1);
+}
+
+// Full-way bounce-back (Section 3.5): the collision of an FWALL cell sends
+// every population back where it came from, f*_i = f_opp(i).
+template <int Q>
+__device__ __forceinline__ void reverse_populations(float (&df)[Q]) {
+#pragma unroll
+  for (int i = 1; i < Q; ++i)
+    if (i < opposite<Q>(i)) {
+      const float t = df[i];
+      df[i] = df[opposite<Q>(i)];
+      df[opposite<Q>(i)] = t;
+    }
+}
+
+template <int Q, typename S, bool FW = true>
 __device__ __forceinline__ void pull_periodic(const S* __restrict__ src, const StepParams& p, const Nbr& nb,
                                               int self, int x, int y, int z, float (&df)[Q]) {
   int fcx[3] = {0, 0, 0}, fcy[3] = {0, 0, 0}, fcz[3] = {0, 0, 0};
@@ -97,16 +125,16 @@ __device__ __forceinline__ void pull_periodic(const S* __restrict__ src, const S
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int t = i == 0 ? 0
-                         : face_combine(fcx[1 - Lattice<Q>::c(i, 0)], fcy[1 - Lattice<Q>::c(i, 1)],
-                                        fcz[1 - Lattice<Q>::c(i, 2)]);
+                         : face_combine<FW>(fcx[1 - Lattice<Q>::c(i, 0)], fcy[1 - Lattice<Q>::c(i, 1)],
+                                            fcz[1 - Lattice<Q>::c(i, 2)]);
     const S* a = t ? src + (long long)opposite<Q>(i) * p.plane + self : base + src_index<Q>(nb, i);
     df[i] = Store<S>::ld(a);
     base += p.plane;
   }
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    const int t = face_combine(fcx[1 - Lattice<Q>::c(i, 0)], fcy[1 - Lattice<Q>::c(i, 1)],
-                               fcz[1 - Lattice<Q>::c(i, 2)]);
+    const int t = face_combine<FW>(fcx[1 - Lattice<Q>::c(i, 0)], fcy[1 - Lattice<Q>::c(i, 1)],
+                                   fcz[1 - Lattice<Q>::c(i, 2)]);
     if (t == EQ) df[i] = p.eq_df[i];
     if (t == LID) df[i] += p.lid_term[i];
   }
@@ -135,12 +163,12 @@ __device__ __forceinline__ void zou_he_inlet(const StepParams& p, float (&df)[Q]
   }
 }
 
-// Post-stream populations of a fluid-like cell.  The pull applies the face
-// rules and reads the ghost values that every other WALL / LID / EQ source
-// carries (see k_boundary), i.e. the bounce-back, moving-wall and equilibrium
-// rules; INLET cells then rebuild their c_x = +1 populations by Zou-He and
-// OUTLET cells copy their c_x = -1 populations from the pull at x - 1
-// (zero-gradient outflow).
+// Post-stream populations of a fluid-like or FWALL cell.  The pull applies
+// the face rules and reads the ghost values that every other WALL / LID / EQ
+// source carries (see k_boundary), i.e. the bounce-back, moving-wall and
+// equilibrium rules; INLET cells then rebuild their c_x = +1 populations by
+// Zou-He and OUTLET cells copy their c_x = -1 populations from the pull at
+// x - 1 (zero-gradient outflow).
 template <int Q, typename S>
 __device__ __forceinline__ void pull_cell(const S* __restrict__ src, const StepParams& p, int x, int y, int z,
                                           int type, const Nbr& nb, float (&df)[Q]) {

@@ -12,8 +12,9 @@ long long row_blocks(const StepParams& p) {
   return nxb * (long long)p.ny * p.nz;
 }
 
-// flags = type | FLAG_SLOW where a fluid-like cell has a non-fluid-like cell
-// in its Q-stencil, or is an INLET / OUTLET cell.  Codes >= 6 set *err.
+// flags = type | FLAG_SLOW where a fluid-like cell has a WALL / LID / EQ cell
+// in its Q-stencil, or is an INLET / OUTLET / FWALL cell.  Codes >= 7 set
+// *err.
 template <int Q>
 __global__ void k_mask_prepare(const uint8_t* __restrict__ mask, uint8_t* __restrict__ flags, int nx, int ny,
                                int nz, int* err) {
@@ -21,12 +22,12 @@ __global__ void k_mask_prepare(const uint8_t* __restrict__ mask, uint8_t* __rest
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
        cell += (long long)gridDim.x * blockDim.x) {
     const int t = mask[cell];
-    if (t > EQ) {
+    if (t > FWALL) {
       atomicExch(err, 1);
       flags[cell] = WALL;
       continue;
     }
-    int slow = (t == INLET || t == OUTLET);
+    int slow = (t == INLET || t == OUTLET || t == FWALL);
     if (fluid_like(t) && !slow) {
       const int x = (int)(cell % nx);
       const long long r = cell / nx;
@@ -39,7 +40,7 @@ __global__ void k_mask_prepare(const uint8_t* __restrict__ mask, uint8_t* __rest
         ys = ys < 0 ? ny - 1 : (ys >= ny ? 0 : ys);
         zs = zs < 0 ? nz - 1 : (zs >= nz ? 0 : zs);
         const int ts = mask[xs + (long long)nx * (ys + (long long)ny * zs)];
-        if (!fluid_like(ts)) slow = 1;
+        if (!holds_state(ts)) slow = 1;
       }
     }
     flags[cell] = (uint8_t)(t | (slow ? FLAG_SLOW : 0));
@@ -67,37 +68,47 @@ int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int 
 // Boundary tables, built once per mask by compaction in two passes per
 // table (per-block counts; an exclusive scan of the counts on the host; then
 // ordered per-block writes):
-//  - links, direction-major: for each direction i in turn, every FLUID cell x
-//    (ascending) whose source x - c_i is WALL, LID or EQ, as {x, i | type << 8}.
-//    Consecutive entries then touch consecutive cells of one population
-//    plane wherever the wall is not normal to x;
-//  - fix-up cells: every INLET and OUTLET cell, ascending.
+//  - links, direction-major: for each direction i in turn, every FLUID cell
+//    and every FWALL cell on an FWALL face plane x (ascending) whose source
+//    x - c_i is WALL, LID or EQ and not on a face plane, as
+//    {x, i | type << 8}.  Consecutive entries then touch consecutive cells of
+//    one population plane wherever the wall is not normal to x;
+//  - fix-up cells: every INLET and OUTLET cell and every FWALL cell off the
+//    face planes, ascending.
 constexpr int LIST_BLOCK = 256;
 
 struct Pred {
-  int mode;        // 0: link in direction (cx, cy, cz); 1: inlet / outlet cell
+  int mode;        // 0: link in direction (cx, cy, cz); 1: fix-up cell
   int cx, cy, cz;  // velocity of the link direction
   int face[6];     // described boundary faces: their sources need no ghost
 };
 
+// Does (x, y, z) lie on one of the described face planes?
+__device__ __forceinline__ bool on_face_plane(int x, int y, int z, int nx, int ny, int nz, const Pred& pr) {
+  return (x == 0 && pr.face[0]) || (x == nx - 1 && pr.face[1]) || (y == 0 && pr.face[2]) ||
+         (y == ny - 1 && pr.face[3]) || (nz > 1 && z == 0 && pr.face[4]) || (nz > 1 && z == nz - 1 && pr.face[5]);
+}
+
 __device__ __forceinline__ int pred_eval(const uint8_t* __restrict__ flags, long long cell, int nx, int ny, int nz,
                                          const Pred& pr, int* type) {
   const int t = flags[cell] & FLAG_TYPE;
-  if (pr.mode == 1) return t == INLET || t == OUTLET;
-  if (t != FLUID) return 0;
+  if (pr.mode == 1 ? !(t == INLET || t == OUTLET || t == FWALL) : !(t == FLUID || t == FWALL)) return 0;
   const int x = (int)(cell % nx);
   const long long r = cell / nx;
   const int y = (int)(r % ny), z = (int)(r / ny);
+  // an FWALL cell on a face plane is updated by the bulk pass (it lies on an
+  // FWALL face: the host keeps a face only where its plane's cells have the
+  // type the faces derive); any other FWALL cell is a fix-up cell
+  const bool fw_face = t == FWALL && on_face_plane(x, y, z, nx, ny, nz, pr);
+  if (pr.mode == 1) return t == INLET || t == OUTLET || (t == FWALL && !fw_face);
+  if (t == FWALL && !fw_face) return 0;
   int xs = x - pr.cx, ys = y - pr.cy, zs = z - pr.cz;
   xs = xs < 0 ? nx - 1 : (xs >= nx ? 0 : xs);
   ys = ys < 0 ? ny - 1 : (ys >= ny ? 0 : ys);
   zs = zs < 0 ? nz - 1 : (zs >= nz ? 0 : zs);
   const int ts = flags[xs + (long long)nx * (ys + (long long)ny * zs)] & FLAG_TYPE;
   *type = ts;
-  const bool on_face = (xs == 0 && pr.face[0]) || (xs == nx - 1 && pr.face[1]) || (ys == 0 && pr.face[2]) ||
-                       (ys == ny - 1 && pr.face[3]) || (nz > 1 && zs == 0 && pr.face[4]) ||
-                       (nz > 1 && zs == nz - 1 && pr.face[5]);
-  return !fluid_like(ts) && !on_face;
+  return !holds_state(ts) && !on_face_plane(xs, ys, zs, nx, ny, nz, pr);
 }
 
 __global__ void k_pred_count(const uint8_t* __restrict__ flags, long long n, int nx, int ny, int nz, Pred pr,

@@ -12,16 +12,23 @@
 namespace xlb {
 
 // Cell types of the mask (Section 3.5); values are the public ABI codes.
-enum CellType : uint8_t { FLUID = 0, WALL = 1, LID = 2, INLET = 3, OUTLET = 4, EQ = 5 };
+// FWALL is a full-way bounce-back wall (the walls of the Section 5 cavity):
+// it is streamed like a fluid cell and its collision reverses every
+// population, so its slots hold real state, never ghost values.
+enum CellType : uint8_t { FLUID = 0, WALL = 1, LID = 2, INLET = 3, OUTLET = 4, EQ = 5, FWALL = 6 };
 
 // Derived per-cell flag byte written by the mask preparation kernel:
 // bits 0-2 hold the cell type, bit 3 marks a fluid-like cell whose update
-// needs the per-direction boundary rules (a non-fluid cell in its stencil, or
-// an inlet / outlet cell itself).
+// needs the per-direction boundary rules (a WALL / LID / EQ cell in its
+// stencil, or an inlet / outlet / FWALL cell itself).
 constexpr uint8_t FLAG_TYPE = 0x07;
 constexpr uint8_t FLAG_SLOW = 0x08;
 
 XLB_HD inline bool fluid_like(int t) { return t == FLUID || t == INLET || t == OUTLET; }
+
+// Cells whose slots hold streamed state (fluid-like and FWALL); the others
+// (WALL, LID, EQ) hold ghost values.
+XLB_HD inline bool holds_state(int t) { return fluid_like(t) || t == FWALL; }
 
 // Everything one stream-collide launch needs besides the two buffers.
 struct StepParams {
@@ -37,10 +44,12 @@ struct StepParams {
   float eq_rho, eq_u[3];
   float inlet_u[3];      // Zou-He inlet velocity
   int* err;              // device error word for kernels with bounded waits
-  // Boundary faces: type (0 = none, WALL, LID or EQ) of each whole face plane
-  // x = 0, x = nx-1, y = 0, y = ny-1, z = 0, z = nz-1 that the mask fills
-  // uniformly (WALL wins where planes meet).  Pulls from such a plane apply
-  // the rule by coordinates; every other non-fluid source uses ghost values.
+  // Boundary faces: type (0 = none, WALL, LID, EQ or FWALL) of each whole
+  // face plane x = 0, x = nx-1, y = 0, y = ny-1, z = 0, z = nz-1 that the
+  // mask fills uniformly (where planes meet WALL wins, then FWALL).  Pulls
+  // from a WALL / LID / EQ plane apply the rule by coordinates, pulls from an
+  // FWALL plane are plain, and cells of an FWALL plane reverse instead of
+  // colliding; every other WALL / LID / EQ source uses ghost values.
   int face[6];
   int has_faces;
 };

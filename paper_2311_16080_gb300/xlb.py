@@ -25,7 +25,7 @@ XLB_D2Q9, XLB_D3Q19, XLB_D3Q27 = 9, 19, 27
 XLB_COLL_NONE, XLB_COLL_BGK, XLB_COLL_KBC = 0, 1, 2
 XLB_STORE_F32, XLB_STORE_F16, XLB_STORE_BF16 = 0, 1, 2
 XLB_KERNEL_AUTO, XLB_KERNEL_DIRECT, XLB_KERNEL_VEC = 0, 1, 2
-XLB_CELL_FLUID, XLB_CELL_WALL, XLB_CELL_LID, XLB_CELL_INLET, XLB_CELL_OUTLET, XLB_CELL_EQ = range(6)
+XLB_CELL_FLUID, XLB_CELL_WALL, XLB_CELL_LID, XLB_CELL_INLET, XLB_CELL_OUTLET, XLB_CELL_EQ, XLB_CELL_FWALL = range(7)
 
 STORAGE = {"f32": XLB_STORE_F32, "f16": XLB_STORE_F16, "bf16": XLB_STORE_BF16}
 COLLISION = {"none": XLB_COLL_NONE, "bgk": XLB_COLL_BGK, "kbc": XLB_COLL_KBC}

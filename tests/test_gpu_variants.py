@@ -31,6 +31,12 @@ def _cases():
     out.append(("periodic27", Case(27, (8, 12, 48), 1.5, "bgk", rho0=r, u0=u)))
     m = I.lid_driven_cavity_mask(72, 10, 12)  # 72 / 4 = 18 slots: partial warps
     out.append(("ragged19", Case(19, m.shape, 1.7, "bgk", mask=m, lid=(1.0, (0.05, 0.0, 0.0)))))
+    m = I.channel_2d_mask(64, 40)  # WALL faces; FWALL obstacles are fix-up cells
+    m[I.random_obstacle_mask(sh, 0.05, seed=7) > 0] = O.FWALL
+    m[0, :] = O.WALL
+    m[-1, :] = O.WALL
+    r, u = I.random_flow(sh, 2, seed=8, rho_amp=0.005, u_amp=0.02)
+    out.append(("fwall9", Case(9, sh, 1.4, "bgk", mask=m, force=(1e-5, 0.0, 0.0), rho0=r, u0=u)))
     return out
 
 
