@@ -261,17 +261,29 @@ class BC:
     """Prescribed values of the mask's boundary types.
 
     lid_u / lid_rho:  moving-wall velocity and fixed wall density (LID cells).
-    inlet_u:          Zou-He inlet velocity (INLET cells).
+    inlet_u:          Zou-He inlet velocity (INLET cells): d constants, or a
+                      field of shape (d, *mask.shape) (a velocity profile).
     eq_rho / eq_u:    equilibrium-BC state (EQ cells).
+    wall_q:           Bouzidi wall distances: None, or an array (Q, *mask.shape)
+                      whose entry [i, x] is the fraction q in (0, 1] of the
+                      link from fluid cell x along c_i at which the wall
+                      crosses it, where x + c_i is a WALL cell; NaN elsewhere
+                      (those links keep halfway bounce-back, q = 1/2).
     """
 
-    def __init__(self, d, lid_u=None, lid_rho=1.0, inlet_u=None, eq_rho=1.0, eq_u=None):
+    def __init__(self, d, lid_u=None, lid_rho=1.0, inlet_u=None, eq_rho=1.0, eq_u=None, wall_q=None):
         z = [0.0] * d
         self.lid_u = list(lid_u) if lid_u is not None else z
         self.lid_rho = lid_rho
-        self.inlet_u = list(inlet_u) if inlet_u is not None else z
+        if inlet_u is None:
+            self.inlet_u = z
+        elif np.ndim(inlet_u) > 1:
+            self.inlet_u = np.asarray(inlet_u, dtype=float)
+        else:
+            self.inlet_u = list(inlet_u)
         self.eq_rho = eq_rho
         self.eq_u = list(eq_u) if eq_u is not None else z
+        self.wall_q = wall_q
 
 
 def _const_feq(lat, rho, u):
@@ -283,10 +295,30 @@ def fluid_like(mask):
     return np.isin(mask, FLUID_LIKE)
 
 
+def bouzidi(lat: Lattice, h, mask, j, q):
+    """Linear interpolated bounce-back of Bouzidi, Firdaouss and Lallemand
+    (2001), the curved-wall no-slip rule Section 4.3 names: the population
+    f_j(x) that a fluid cell x pulls from a WALL cell x - c_j, when the wall
+    crosses the link from x along c_i = -c_j at the fraction q of its length:
+      q <  1/2:  f_j(x) = 2q h_i(x) + (1 - 2q) h_i(x + c_j)
+      q >= 1/2:  f_j(x) = h_i(x) / (2q) + (2q - 1) / (2q) h_j(x)
+    (h: post-collision populations).  Where q < 1/2 but x + c_j is not a
+    FLUID cell the halfway value h_i(x) is kept.  Returns the field of f_j
+    values for every x (meaningful where q is finite)."""
+    i = lat.opp[j]
+    behind = lat.roll(h[i], i)               # h_i(x - c_i) = h_i(x + c_j)
+    behind_fl = lat.roll(mask, i) == FLUID
+    with np.errstate(invalid="ignore", divide="ignore"):
+        low = np.where(behind_fl, 2.0 * q * h[i] + (1.0 - 2.0 * q) * behind, h[i])
+        high = h[i] / (2.0 * q) + (2.0 * q - 1.0) / (2.0 * q) * h[j]
+    return np.where(q < 0.5, low, high)
+
+
 def pull_plain(lat: Lattice, h, mask, bc: BC):
     """Post-stream populations from post-collision ones, before the inlet and
     outlet rules: f_i(x) = h_i(x - c_i) with periodic wrap (Eq. 2), except that
-    a source cell x - c_i of type WALL gives h_opp(i)(x), LID gives
+    a source cell x - c_i of type WALL gives h_opp(i)(x) (or the Bouzidi value
+    where bc.wall_q gives the link a wall distance), LID gives
     h_opp(i)(x) + 2 w_i rho_w (c_i . u_w) / cs2, and EQ gives f_i^eq(rho_w, u_w)."""
     feq_w = _const_feq(lat, bc.eq_rho, bc.eq_u)
     out = []
@@ -295,6 +327,9 @@ def pull_plain(lat: Lattice, h, mask, bc: BC):
         src = lat.roll(mask, i)
         hb = h[lat.opp[i]]
         cu_lid = sum(lat.c[i, a] * bc.lid_u[a] for a in range(lat.d))
+        if bc.wall_q is not None and i != 0:
+            q = bc.wall_q[lat.opp[i]]
+            hb = np.where(np.isfinite(q), bouzidi(lat, h, mask, i, q), hb)
         g = np.where(src == WALL, hb, g)
         g = np.where(src == LID, hb + 2.0 * lat.w[i] * bc.lid_rho * cu_lid / CS2, g)
         g = np.where(src == EQ, feq_w[i], g)
@@ -312,10 +347,10 @@ def zou_he_inlet(lat: Lattice, f, mask, bc: BC):
     if not sel.any():
         return f
     f = f.copy()
-    ux = bc.inlet_u[0]
+    uin = np.stack([np.broadcast_to(np.asarray(bc.inlet_u[a], dtype=float), mask.shape)
+                    for a in range(lat.d)])
     rho = (sum(f[i] for i in range(lat.q) if cx[i] == 0)
-           + 2.0 * sum(f[i] for i in range(lat.q) if cx[i] == -1)) / (1.0 - ux)
-    uin = np.stack([np.full(mask.shape, bc.inlet_u[a]) for a in range(lat.d)])
+           + 2.0 * sum(f[i] for i in range(lat.q) if cx[i] == -1)) / (1.0 - uin[0])
     feq = equilibrium(lat, rho, uin)
     for i in range(lat.q):
         if cx[i] == 1:
@@ -554,6 +589,27 @@ def gradient_init(lat: Lattice, rho0, u0, mask, p: Params, n, seed_fn):
 
 # ---------------------------------------------------------------------------
 # Reductions used by the invariant checks
+
+def wall_force(lat: Lattice, f, mask, p: Params, solid=None):
+    """Momentum-exchange force on the WALL cells (Mei et al. 2002, in the
+    form Caiazzo and Junk 2008 give for interpolated walls, the method Section
+    4.3 names) at the step of the post-stream state f: with h = C(f) and
+    f' = S_bc(h) the next post-stream state,
+      F = sum over links (x, i), x FLUID, x + c_i a WALL cell in `solid`
+          (all WALL cells if None), of c_i [h_i(x) + f'_opp(i)(x)],
+    the momentum the populations crossing each link hand to the wall."""
+    h = collide(lat, f, mask, p)
+    fn = stream_bc(lat, h, mask, p.bc)
+    sel = (mask == WALL) if solid is None else ((mask == WALL) & solid)
+    F = np.zeros(lat.d)
+    for i in range(1, lat.q):
+        tgt = lat.roll(sel.astype(np.uint8), i, sign=-1).astype(bool)   # x + c_i selected
+        link = (mask == FLUID) & tgt
+        v = np.where(link, h[i] + fn[lat.opp[i]], 0.0)
+        for a in range(lat.d):
+            F[a] += lat.c[i, a] * float(np.real(v.sum()))
+    return F
+
 
 def total_mass(lat: Lattice, f, mask):
     return float(np.real(density(lat, f)[fluid_like(mask)].sum()))

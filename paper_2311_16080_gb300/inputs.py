@@ -82,6 +82,73 @@ def sphere_channel_mask(nx, ny, nz, radius, center=None):
     return m
 
 
+def schafer_turek_2d(n_d, u_mean):
+    """The 2D flow-around-a-cylinder benchmark of Schafer and Turek (1996)
+    that Section 4.3 uses: channel 2.2 x 0.41, cylinder of diameter D = 0.1
+    centred at (0.2, 0.2), parabolic inflow of mean speed U; n_d cells per D.
+
+    Cells: WALL rows y = 0 and ny - 1 (no-slip lines half a cell inside, at
+    y = 1/2 and ny - 3/2, so the channel is H = 4.1 n_d cells high), INLET
+    column x = 0, OUTLET column x = nx - 1 = 22 n_d, cylinder cells WALL where
+    the cell centre lies within D/2 of (2 n_d, 2 n_d + 1/2).
+    Returns (mask[ny, nx], center (x, y), radius, inlet velocity field
+    u[2, ny, nx] = (4 U_m y' (H - y') / H^2, 0) with y' = y - 1/2 and
+    U_m = 3 U / 2)."""
+    H = round(4.1 * n_d)
+    ny, nx = H + 2, 22 * n_d + 1
+    center = (2.0 * n_d, 2.0 * n_d + 0.5)
+    radius = 0.5 * n_d
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    m = np.zeros((ny, nx), dtype=np.uint8)
+    m[(x - center[0]) ** 2 + (y - center[1]) ** 2 <= radius * radius] = WALL
+    m[1:ny - 1, 0] = INLET
+    m[1:ny - 1, nx - 1] = OUTLET
+    m[0, :] = WALL
+    m[ny - 1, :] = WALL
+    yp = np.arange(ny) - 0.5
+    prof = 4.0 * 1.5 * u_mean * yp * (H - yp) / (H * H)
+    prof[0] = prof[ny - 1] = 0.0
+    u = np.zeros((2, ny, nx))
+    u[0] = prof[:, None]
+    return m, center, radius, u
+
+
+def ball_links(mask, center, radius, c):
+    """Links from FLUID cells to the cells of a disc / ball (cell centres
+    within `radius` of `center` = (x, y[, z])), with the fraction q in (0, 1]
+    of each link at which it enters the circle / sphere.  c: the lattice
+    velocities (Q x d, Figure 1 order).  Returns (cells as flat indices, x
+    fastest; directions; q)."""
+    d = mask.ndim
+    c = np.asarray(c)
+    coords = np.meshgrid(*[np.arange(n) for n in mask.shape], indexing="ij")
+    pos = [coords[d - 1 - a] for a in range(d)]          # x, y[, z]
+    ctr = np.asarray(center, dtype=float)
+    inside = sum((pos[a] - ctr[a]) ** 2 for a in range(d)) <= radius * radius
+    cells, dirs, qs = [], [], []
+    fl = np.argwhere(mask == FLUID)
+    for i in range(1, c.shape[0]):
+        ci = c[i, :d]
+        tgt = fl[:, ::-1] + ci                            # (x, y[, z]) of x + c_i
+        ok = np.all((tgt >= 0) & (tgt < np.array(mask.shape[::-1])), axis=1)
+        src, tgt = fl[ok], tgt[ok]
+        hit = inside[tuple(tgt[:, ::-1].T)] & (mask[tuple(tgt[:, ::-1].T)] == WALL)
+        src = src[hit]
+        if not len(src):
+            continue
+        r0 = src[:, ::-1].astype(float) - ctr                 # x - C
+        a = float(ci @ ci)
+        b = 2.0 * (r0 @ ci)
+        cc = (r0 * r0).sum(axis=1) - radius * radius
+        t = (-b - np.sqrt(b * b - 4.0 * a * cc)) / (2.0 * a)
+        cells.append(np.ravel_multi_index(tuple(src.T), mask.shape))
+        dirs.append(np.full(len(src), i))
+        qs.append(t)
+    if not cells:
+        return np.zeros(0, np.int64), np.zeros(0, np.int32), np.zeros(0)
+    return np.concatenate(cells).astype(np.int64), np.concatenate(dirs).astype(np.int32), np.concatenate(qs)
+
+
 def channel_2d_mask(nx, ny, top=WALL, bottom=WALL):
     """2D channel periodic in x with solid rows y = 0 and y = ny-1."""
     m = np.zeros((ny, nx), dtype=np.uint8)

@@ -258,6 +258,114 @@ def test_paper_cavity_mirror_symmetry():
     np.testing.assert_allclose(uu[2], uu[2][:, ::-1, :], rtol=0, atol=1e-13)
 
 
+def _bouzidi_channel(ny, qb, qt, omega, F=1e-5, steps=4000):
+    """D2Q9 force-driven channel, WALL rows y = 0 and ny - 1, with Bouzidi
+    walls crossing the wall-ward links at fractions qb (bottom) and qt (top):
+    the no-slip lines lie at y = 1 - qb and y = ny - 2 + qt."""
+    lat = O.Lattice(9)
+    mask = I.channel_2d_mask(4, ny)
+    q = np.full((9,) + mask.shape, np.nan)
+    for i in range(9):
+        if lat.c[i, 1] == -1:
+            q[i, 1, :] = qb
+        if lat.c[i, 1] == 1:
+            q[i, ny - 2, :] = qt
+    nu = O.nu_from_omega(omega)
+    p = O.Params(lat, omega, force=(F, 0.0), bc=O.BC(2, wall_q=q))
+    y = np.arange(ny)
+    ref = F / (2 * nu) * (y - (1 - qb)) * (ny - 2 + qt - y)
+    rho = np.ones(mask.shape)
+    u = np.zeros((2,) + mask.shape)
+    u[0, 1:ny - 1, :] = ref[1:ny - 1, None]
+    f = O.run(lat, O.init_state(lat, rho, u, mask, p), mask, p, steps)
+    _, uu = O.macroscopic(lat, f, mask, p)
+    err = np.max(np.abs(uu[0, 1:ny - 1, 2] - ref[1:ny - 1])) / ref.max()
+    return err, O.wall_force(lat, f, mask, p), F * int((mask == O.FLUID).sum())
+
+
+def test_bouzidi_half_is_halfway_bounce_back():
+    """q = 1/2 on every wall link reduces Bouzidi to halfway bounce-back
+    exactly, from either branch's side."""
+    lat = O.Lattice(19)
+    rng = np.random.default_rng(61)
+    shape = (5, 6, 7)
+    mask = np.where(rng.random(shape) < 0.2, O.WALL, O.FLUID).astype(np.uint8)
+    h = lat.w[:, None, None, None] * (1 + 0.1 * rng.standard_normal((19,) + shape))
+    plain = O.pull_plain(lat, h, mask, O.BC(3))
+    for qv, tol in ((0.5, 0.0), (0.5 - 1e-13, 1e-12)):
+        bq = O.pull_plain(lat, h, mask, O.BC(3, wall_q=np.full((19,) + shape, qv)))
+        assert np.max(np.abs(bq - plain)) <= tol
+
+
+def test_bouzidi_bruteforce():
+    """The interpolated rule of Bouzidi et al. (2001), per-cell loops on a
+    D2Q9 grid with random WALL cells and random wall distances."""
+    lat = O.Lattice(9)
+    ny, nx = 6, 7
+    rng = np.random.default_rng(62)
+    mask = np.where(rng.random((ny, nx)) < 0.25, O.WALL, O.FLUID).astype(np.uint8)
+    h = rng.standard_normal((9, ny, nx))
+    q = rng.uniform(0.05, 1.0, (9, ny, nx))
+    q[rng.random((9, ny, nx)) < 0.2] = np.nan
+    f = O.pull_plain(lat, h, mask, O.BC(2, wall_q=q))
+    for j in range(1, 9):
+        cx, cy = (int(v) for v in lat.c[j])
+        i = int(lat.opp[j])
+        for y in range(ny):
+            for x in range(nx):
+                if mask[(y - cy) % ny, (x - cx) % nx] != O.WALL:
+                    continue
+                qq = q[i, y, x]
+                if not np.isfinite(qq):
+                    ref = h[i, y, x]
+                elif qq < 0.5:
+                    by, bx = (y + cy) % ny, (x + cx) % nx
+                    ref = (2 * qq * h[i, y, x] + (1 - 2 * qq) * h[i, by, bx]
+                           if mask[by, bx] == O.FLUID else h[i, y, x])
+                else:
+                    ref = h[i, y, x] / (2 * qq) + (2 * qq - 1) / (2 * qq) * h[j, y, x]
+                assert abs(f[j, y, x] - ref) <= 1e-14 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("qb,qt", [(0.25, 0.75), (0.1, 0.9)])
+def test_bouzidi_poiseuille_second_order(qb, qt):
+    """Channel flow between Bouzidi walls placed off the halfway points: the
+    error against the parabola through the true wall positions falls by
+    about 4 when the width doubles (second order).  Halfway bounce-back
+    (walls at the wrong place) would give a first-order error."""
+    e1 = _bouzidi_channel(18, qb, qt, 1.0, steps=2500)[0]
+    e2 = _bouzidi_channel(34, qb, qt, 1.0, steps=7000)[0]
+    assert e1 < 0.02 and 3.5 < e1 / e2 < 4.5
+
+
+def test_wall_force_balances_body_force():
+    """Steady channel flow: the momentum-exchange force on the walls equals
+    the body force on all fluid cells (the momentum balance), for halfway and
+    for Bouzidi walls."""
+    for qb, qt in ((0.5, 0.5), (0.3, 0.8)):
+        _, Fw, Fb = _bouzidi_channel(18, qb, qt, 1.0, steps=3000)
+        assert abs(Fw[0] - Fb) <= 1e-9 * Fb and abs(Fw[1]) <= 1e-12
+
+
+def test_zou_he_inlet_profile_identity():
+    """With a velocity profile u_in(y) the Zou-He density and populations
+    give rho u_x = j_x and rho = sum f at every inlet cell."""
+    lat = O.Lattice(9)
+    ny, nx = 12, 10
+    mask = I.channel_2d_mask(nx, ny)
+    mask[1:ny - 1, 0] = O.INLET
+    y = np.arange(ny)
+    prof = np.zeros((2, ny, nx))
+    prof[0] = (0.06 * (y - 0.5) * (ny - 1.5 - y) / ((ny - 2) / 2) ** 2)[:, None]
+    rng = np.random.default_rng(63)
+    f = lat.w[:, None, None] * (1 + 0.05 * rng.standard_normal((9, ny, nx)))
+    g = O.zou_he_inlet(lat, f, mask, O.BC(2, inlet_u=prof))
+    sel = mask == O.INLET
+    rho = O.density(lat, g)
+    j = O.momentum(lat, g)
+    np.testing.assert_allclose(j[0][sel], rho[sel] * prof[0][sel], rtol=0, atol=1e-15)
+
+
 def test_kbc_gamma_two_is_bgk():
     for q, shape in ((9, (5, 6)), (27, (3, 4, 5))):
         lat = O.Lattice(q)
