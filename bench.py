@@ -291,7 +291,7 @@ def extras(args, torch, X, I, stream):
 
     # KBC D3Q27 flow past a sphere, 512 x 256 x 256, Zou-He inlet + outflow
     mask = I.sphere_channel_mask(512, 256, 256, radius=32, center=(128, 128, 128))
-    for st in ("f32", "f16"):
+    for st in ("f32", "f16", "bf16"):
         sim = X.Simulation(27, (512, 256, 256), 1.857, "kbc", st, stream=stream.cuda_stream)
         sim.set_mask(mask)
         sim.set_bc(X.XLB_CELL_INLET, 1.0, (0.04, 0.0, 0.0))
@@ -303,6 +303,31 @@ def extras(args, torch, X, I, stream):
         res[f"kbc_d3q27_sphere_{st}_algo_GBs"] = round(2 * 27 * (4 if st == "f32" else 2) * cells / (ms * 1e-3) / 1e9, 1)
         sim.close()
     del mask
+
+    # the same flow on the 128 x 64 x 64 crop (radius 8), 1000 steps, in the
+    # three storage forms, against the FP64 oracle's velocity stored at
+    # 16,384 sampled fluid cells by tests/golden/make_kbc_sphere_crop.py
+    try:
+        import importlib.util
+        path = os.path.join(ROOT, "tests", "golden", "make_kbc_sphere_crop.py")
+        spec = importlib.util.spec_from_file_location("make_kbc_sphere_crop", path)
+        crop = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(crop)
+        ref = np.load(crop.OUT)
+        _, cmask, crho, cu, _ = crop.setup()
+        for st in ("f32", "f16", "bf16"):
+            sim = X.Simulation(27, (crop.NX, crop.NY, crop.NZ), crop.OMEGA, "kbc", st, stream=stream.cuda_stream)
+            sim.set_mask(cmask)
+            sim.set_bc(X.XLB_CELL_INLET, 1.0, (crop.U_IN, 0.0, 0.0))
+            sim.init(crho.astype(np.float32), cu.astype(np.float32))
+            sim.step(int(ref["steps"]))
+            _, ug = sim.macroscopic()
+            sim.close()
+            got = ug.reshape(3, -1)[:, ref["index"]].astype(np.float64)
+            res[f"kbc_crop128_{st}_rel_l2_u_sampled"] = float(np.sqrt(((got - ref["u"]) ** 2).sum()
+                                                                        / (ref["u"] ** 2).sum()))
+    except Exception as e:  # secondary figures; keep the line
+        res["kbc_crop128_error"] = repr(e)
 
     # adjoint: D3Q19 128^3 periodic, 500 steps, checkpoints every 50; the
     # gradient is computed twice on one context and the second (warm: the
@@ -383,6 +408,26 @@ def extras(args, torch, X, I, stream):
     res["batch4096_persistent_5000_steps_s"] = round(ms / 1e3, 3)
     bt.close()
 
+    # Taylor-Green 128^2 D2Q9 FP32 (16,384 cells: launch-bound), 1000 steps:
+    # one launch per update against graph replay of 100 updates per graph
+    nt = 128
+    r0, u0 = I.taylor_green_2d(nt, nt, 0.04)
+    for mode, g in (("launch", 0), ("graph", 100)):
+        s = X.Simulation(9, (nt, nt), 1.25, "bgk", "f32", stream=stream.cuda_stream)
+        s.set_step_graph(g)
+        s.init(r0.astype(np.float32), u0.astype(np.float32))
+        s.step(201)  # local collision, then a capture and a replay
+        ms = timed(s, 1000)
+        res[f"tg128_f32_{mode}_mlups"] = round(nt * nt / (ms * 1e3), 1)
+        s.close()
+
+    # Section 4.3's cylinder: Schafer-Turek 2D at Re = 100, 80 cells per
+    # diameter, u = 0.003, to t = 100 D/U (2.67 M steps), C_d, C_l, St
+    try:
+        res.update(schafer_turek(torch, X, I, stream))
+    except Exception as e:  # secondary figures; keep the line
+        res["schafer_turek_error"] = repr(e)
+
     # storage error: Taylor-Green 128^2, 1000 steps, against the FP64 oracle
     try:
         from oracle import lbm as O
@@ -404,6 +449,58 @@ def extras(args, torch, X, I, stream):
     except Exception as e:  # the error figures are secondary; keep the line
         res["tg128_error"] = repr(e)
     return res
+
+
+def schafer_turek(torch, X, I, stream, n_d=80, u=0.003, re=100.0, t_end=100.0, every=100):
+    """The flow around a cylinder of Section 4.3 (Schafer-Turek 2D benchmark):
+    BGK, Bouzidi walls on the cylinder, regularized Poiseuille inflow,
+    outflow, halfway channel walls, FP32; the momentum-exchange force is
+    recorded on the device every `every` steps (graph replay in between).
+    Maxima of C_d, C_l and the Strouhal number over 50 <= t <= 100."""
+    c, _ = X.xlb_lattice_table(9)
+    m, ctr, radius, uin = I.schafer_turek_2d(n_d, u)
+    cells, dirs, q = I.ball_links(m, ctr, radius, c[:, :2])
+    omega = 1.0 / (3.0 * u * n_d / re + 0.5)
+    ny, nx = m.shape
+    sim = X.Simulation(9, (nx, ny), omega, "bgk", "f32", stream=stream.cuda_stream)
+    sim.set_mask(m)
+    sim.set_inlet_profile(uin.astype(np.float32))
+    sim.set_inlet_scheme("regularized")
+    sim.set_wall_distances(cells, dirs, q.astype(np.float32))
+    u0 = (uin * np.isin(m, (0, 3, 4))).astype(np.float32)
+    sim.init(np.ones(m.shape, np.float32), u0)
+    sim.set_step_graph(every)
+    steps = int(round(t_end * n_d / u))
+    n = steps // every
+    F = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    base = F.data_ptr()
+    sim.step(1)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(n):
+        sim.step(every)
+        sim.wall_force(base + 24 * k)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    sim.close()
+    Fh = F.cpu().numpy()
+    t = (1 + every * (np.arange(n) + 1)) * u / n_d
+    cd = 2.0 * Fh[:, 0] / (u * u * n_d)
+    cl = 2.0 * Fh[:, 1] / (u * u * n_d)
+    win = t >= 50.0
+    x = cl[win] - cl[win].mean()
+    tw = t[win]
+    k = np.flatnonzero((x[:-1] < 0) & (x[1:] >= 0))
+    tc = tw[k] - x[k] * (tw[k + 1] - tw[k]) / (x[k + 1] - x[k])
+    st = (len(tc) - 1) / (tc[-1] - tc[0]) if len(tc) > 1 else float("nan")
+    return {"schafer_turek_re100_cd_max": round(float(cd[win].max()), 4),
+            "schafer_turek_re100_cl_max": round(float(cl[win].max()), 4),
+            "schafer_turek_re100_strouhal": round(float(st), 4),
+            "schafer_turek_re100_paper": {"cd_max": 3.25, "cl_max": 0.985, "strouhal": 0.300},
+            "schafer_turek_re100_steps": steps, "schafer_turek_re100_cells": int(m.size),
+            "schafer_turek_re100_s": round(ms / 1e3, 2),
+            "schafer_turek_re100_mlups": round(m.size * steps * 1.0 / (ms * 1e3), 1)}
 
 
 # ---------------------------------------------------------------------------
@@ -428,21 +525,39 @@ def _oracle_cavity_steps(n, steps_or_seconds, by_time):
     return done, el
 
 
-def cpu_baseline(seconds=15.0, n=48):
-    """Oracle timed on the host on a bounded sample of the workload, in a
-    single-threaded child process (numpy / BLAS pinned to one thread)."""
+def _oracle_procs(k, seconds, n):
+    """k concurrent single-threaded child processes, each timing the oracle
+    on its own n^3 cavity for `seconds`; returns [(steps, elapsed), ...]."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench, json; "
             f"d, el = bench._oracle_cavity_steps({n}, {seconds}, True); print(json.dumps([d, el]))")
+    procs = [subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                              stderr=subprocess.DEVNULL, text=True) for _ in range(k)]
+    out = []
+    for pr in procs:
+        so, _ = pr.communicate(timeout=seconds * 6 + 180)
+        out.append(tuple(json.loads(so.strip().splitlines()[-1])))
+    return out
+
+
+def cpu_baseline(seconds=15.0, n=48):
+    """Oracle timed on the host cores on a bounded sample of the workload:
+    one single-threaded child process, then one per core at once (independent
+    n^3 cavities; the oracle itself is not parallelised), whose summed
+    throughput is the all-core figure reported as the value."""
+    cores = os.cpu_count() or 1
     try:
-        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                           timeout=seconds * 6 + 120)
-        done, el = json.loads(r.stdout.strip().splitlines()[-1])
+        (d1, e1), = _oracle_procs(1, seconds, n)
+        allc = _oracle_procs(cores, seconds, n)
     except Exception as e:
-        return {"value": None, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": f"failed: {e!r}"}
-    return {"value": round(n ** 3 * done / (el * 1e6), 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{n}^3 lid-driven cavity (same mask recipe, omega and lid), {done} steps, {el:.1f} s, "
-                      "FP64 numpy oracle, one thread"}
+        return {"value": None, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": f"failed: {e!r}"}
+    single = n ** 3 * d1 / (e1 * 1e6)
+    total = sum(n ** 3 * d / (el * 1e6) for d, el in allc)
+    return {"value": round(total, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "single_thread_value": round(single, 4),
+            "sample": f"{n}^3 lid-driven cavity (same mask recipe, omega and lid), FP64 numpy oracle, ~{seconds:.0f} s: "
+                      f"{cores} concurrent one-thread processes (sum of their MLUPS; {sum(d for d, _ in allc)} steps "
+                      f"in total) and, alone, one thread ({d1} steps in {e1:.1f} s)"}
 
 
 def run_reference(args, rank, world):

@@ -101,6 +101,13 @@ const char* xlb_last_error(const xlb_ctx* ctx);
 /* Static name of a status code. */
 const char* xlb_status_string(int status);
 
+/* The velocity set of a lattice in the library's direction order (Figure 1,
+ * rest velocity first), the order every direction index of this API uses:
+ * c receives 3*Q ints (c_x, c_y, c_z per direction; c_z = 0 on D2Q9) and w,
+ * if not NULL, the Q weights.  Host memory; XLB_ERR_ARG for a lattice other
+ * than 9, 19, 27.  Needs no GPU. */
+int xlb_lattice_table(int lattice, int32_t* c, double* w);
+
 /* omega = 1 / (nu / cs^2 + 1/2) with dt = 1 (Eq. 4). */
 double xlb_omega_from_nu(double nu);
 
@@ -121,6 +128,57 @@ int xlb_set_mask(xlb_ctx* ctx, const uint8_t* mask);
  * cell's slot for that direction (a ghost value, so the next update can pull
  * every cell as if periodic) and recomputes the fix-up cells. */
 int xlb_boundary_links(const xlb_ctx* ctx, int64_t* n_links, int64_t* n_fix);
+
+/* Zou-He inlet velocity per cell (a velocity profile, e.g. the Poiseuille
+ * inflow of the Section 4.3 cylinder): u holds D*N floats, component-major
+ * (u_x of every cell, then u_y, ...; host or device memory, copied); only the
+ * entries of INLET cells are used.  NULL returns to the constant velocity of
+ * xlb_set_bc(XLB_CELL_INLET).  Acts from the next step on.  XLB_ERR_STATE
+ * while a tape is open. */
+int xlb_set_inlet_profile(xlb_ctx* ctx, const float* u);
+
+/* Rule of the INLET cells (Section 4.3 names both): XLB_INLET_ZOU_HE (the
+ * default; non-equilibrium bounce-back of each unknown c_x = +1 population:
+ * f_i = f_opp(i) + f_i^eq - f_opp(i)^eq with rho from the known populations)
+ * or XLB_INLET_REGULARIZED (Latt et al. 2008: the same rho; the unknown
+ * populations' non-equilibrium parts by bounce-back; then every population is
+ * rebuilt as f_i^eq(rho, u) + w_i / (2 cs^4) (c_i c_i - cs^2 I) : Pi^neq).
+ * Acts from the next step on; XLB_ERR_ARG for an unknown scheme,
+ * XLB_ERR_STATE while a tape is open. */
+enum { XLB_INLET_ZOU_HE = 0, XLB_INLET_REGULARIZED = 1 };
+int xlb_set_inlet_scheme(xlb_ctx* ctx, int scheme);
+
+/* Curved no-slip walls: Bouzidi's linear interpolated bounce-back (Bouzidi,
+ * Firdaouss and Lallemand 2001, named in Section 4.3) on listed links.
+ * Link k joins FLUID cell cell[k] (index x + nx*(y + ny*z)) to its WALL
+ * neighbour cell[k] + c_dir[k] (dir[k] in 1..Q-1, Figure 1 order); the wall
+ * crosses the link at the fraction q[k] in [0, 1] of its length from the
+ * fluid cell.  With h the post-collision state and j = opp(dir[k]) the
+ * direction the fluid cell then pulls from the wall cell:
+ *   q <  1/2: f_j(x) = 2q h_i(x) + (1 - 2q) h_i(x + c_j), i = dir[k]
+ *             (h_i(x) if x + c_j is not FLUID),
+ *   q >= 1/2: f_j(x) = h_i(x) / (2q) + (2q - 1) / (2q) h_j(x).
+ * Unlisted WALL links keep halfway bounce-back (q = 1/2).  Arrays are host
+ * memory; the list replaces any earlier one (n = 0 clears it) and acts from
+ * the next step on; a new mask clears it.  XLB_ERR_ARG (nothing changed) if
+ * a link is not a ghost link of the mask (the cell is not FLUID, the
+ * neighbour is not WALL, or the neighbour lies on a boundary face plane) or
+ * a q is outside [0, 1]; XLB_ERR_STATE before a mask or while a tape is open. */
+int xlb_set_wall_distances(xlb_ctx* ctx, int64_t n, const int64_t* cell, const int32_t* dir, const float* q);
+
+/* Momentum-exchange force on the WALL cells off the boundary faces (Mei et
+ * al. 2002 as Caiazzo and Junk 2008 apply it to interpolated walls; the lift
+ * and drag of Section 4.3) in the most recent update, from step t-1 to the
+ * current step t: the sum over the ghost links (FLUID cell x, WALL cell
+ * x + c_i) of c_i [h_i(x, t-1) + f_opp(i)(x, t)], with h the post-collision
+ * populations of step t-1 and f the post-stream populations of step t,
+ * summed in FP64.  out receives 3 doubles (F_z = 0 on D2Q9); a device pointer is
+ * written asynchronously on the ctx stream (for a time series without host
+ * round trips), a host pointer synchronously.  Links of INLET / OUTLET /
+ * FWALL cells and walls on the boundary faces are not included.
+ * XLB_ERR_STATE before the first step after xlb_init (or after a change of
+ * mask or boundary values, until the next step). */
+int xlb_wall_force(xlb_ctx* ctx, double* out);
 
 /* Prescribed state of a boundary type: XLB_CELL_LID (rho_w, u_w of the
  * moving wall), XLB_CELL_INLET (Zou-He velocity u; rho ignored) or
@@ -143,6 +201,18 @@ int xlb_init(xlb_ctx* ctx, const float* rho, const float* u);
  * Asynchronous.  While a tape is open (xlb_tape_begin) the checkpoints of the
  * tape are recorded and stepping past its length is XLB_ERR_STATE. */
 int xlb_step(xlb_ctx* ctx, int64_t n);
+
+/* Graph replay of the update (for small lattices, where launch overhead
+ * dominates): with steps_per_graph = g >= 1, xlb_step advances in blocks of
+ * g updates by launching a CUDA graph of them, captured on the ctx stream at
+ * first use and captured again after any change of the mask, boundary
+ * values, force or kernel variant; the first update after xlb_init and any
+ * remainder of fewer than g updates are launched directly.  g = 0 (the
+ * default) launches every update.  Results are identical either way.  The
+ * capture needs the ctx stream idle and not capturing, with no other thread
+ * queuing work on it during xlb_step; graphs are not used while a tape is
+ * open or profiling is on.  XLB_ERR_ARG for g outside [0, 100000]. */
+int xlb_set_step_graph(xlb_ctx* ctx, int64_t steps_per_graph);
 
 /* Number of steps taken since xlb_init / xlb_state_set. */
 int xlb_get_time(const xlb_ctx* ctx, int64_t* t);

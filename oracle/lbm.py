@@ -265,13 +265,16 @@ class BC:
                       field of shape (d, *mask.shape) (a velocity profile).
     eq_rho / eq_u:    equilibrium-BC state (EQ cells).
     wall_q:           Bouzidi wall distances: None, or an array (Q, *mask.shape)
-                      whose entry [i, x] is the fraction q in (0, 1] of the
+                      whose entry [i, x] is the fraction q in [0, 1] of the
                       link from fluid cell x along c_i at which the wall
                       crosses it, where x + c_i is a WALL cell; NaN elsewhere
                       (those links keep halfway bounce-back, q = 1/2).
+    inlet_scheme:     "zou_he" or "regularized", the two inflow rules Section
+                      4.3 names for INLET cells.
     """
 
-    def __init__(self, d, lid_u=None, lid_rho=1.0, inlet_u=None, eq_rho=1.0, eq_u=None, wall_q=None):
+    def __init__(self, d, lid_u=None, lid_rho=1.0, inlet_u=None, eq_rho=1.0, eq_u=None, wall_q=None,
+                 inlet_scheme="zou_he"):
         z = [0.0] * d
         self.lid_u = list(lid_u) if lid_u is not None else z
         self.lid_rho = lid_rho
@@ -284,6 +287,7 @@ class BC:
         self.eq_rho = eq_rho
         self.eq_u = list(eq_u) if eq_u is not None else z
         self.wall_q = wall_q
+        self.inlet_scheme = inlet_scheme  # "zou_he" | "regularized"
 
 
 def _const_feq(lat, rho, u):
@@ -359,6 +363,36 @@ def zou_he_inlet(lat: Lattice, f, mask, bc: BC):
     return f
 
 
+def regularized_inlet(lat: Lattice, f, mask, bc: BC):
+    """Regularized velocity inlet of Latt et al. (2008), the second inflow
+    rule Section 4.3 names, on INLET cells (inflow along +x, unknowns c_x = +1):
+      rho as in the Zou-He rule; f^neq_i = f_i - f_i^eq(rho, u) for the known
+      populations and f^neq_i = f^neq_opp(i) for the unknown ones;
+      Pi = sum_i c_i c_i f^neq_i; then every population is replaced by
+      f_i = f_i^eq(rho, u) + w_i / (2 cs^4) (c_i c_i - cs^2 I) : Pi."""
+    cx = lat.c[:, 0]
+    sel = mask == INLET
+    if not sel.any():
+        return f
+    uin = np.stack([np.broadcast_to(np.asarray(bc.inlet_u[a], dtype=float), mask.shape)
+                    for a in range(lat.d)])
+    rho = (sum(f[i] for i in range(lat.q) if cx[i] == 0)
+           + 2.0 * sum(f[i] for i in range(lat.q) if cx[i] == -1)) / (1.0 - uin[0])
+    feq = equilibrium(lat, rho, uin)
+    neq = f - feq
+    for i in range(lat.q):
+        if cx[i] == 1:
+            neq[i] = neq[lat.opp[i]]
+    Pi = [[sum(lat.c[i, a] * lat.c[i, b] * neq[i] for i in range(lat.q)) for b in range(lat.d)]
+          for a in range(lat.d)]
+    out = f.copy()
+    for i in range(lat.q):
+        qpi = sum((lat.c[i, a] * lat.c[i, b] - (CS2 if a == b else 0.0)) * Pi[a][b]
+                  for a in range(lat.d) for b in range(lat.d))
+        out[i] = np.where(sel, feq[i] + lat.w[i] / (2.0 * CS2 * CS2) * qpi, f[i])
+    return out
+
+
 def outflow(lat: Lattice, f_plain, f, mask):
     """Zero-gradient outflow on OUTLET cells: populations with c_x = -1 take
     the value that the pull rule gives at the cell x - 1.  Parity unpinned:
@@ -378,7 +412,7 @@ def outflow(lat: Lattice, f_plain, f, mask):
 def stream_bc(lat: Lattice, h, mask, bc: BC):
     """S_bc: the pull stream with every boundary rule of the mask applied."""
     fp = pull_plain(lat, h, mask, bc)
-    f = zou_he_inlet(lat, fp, mask, bc)
+    f = (regularized_inlet if bc.inlet_scheme == "regularized" else zou_he_inlet)(lat, fp, mask, bc)
     f = outflow(lat, fp, f, mask)
     # non-fluid cells carry fixed values: EQ cells f^eq(rho_w, u_w), solids a
     # rest state that no rule ever reads.
@@ -593,8 +627,8 @@ def gradient_init(lat: Lattice, rho0, u0, mask, p: Params, n, seed_fn):
 def wall_force(lat: Lattice, f, mask, p: Params, solid=None):
     """Momentum-exchange force on the WALL cells (Mei et al. 2002, in the
     form Caiazzo and Junk 2008 give for interpolated walls, the method Section
-    4.3 names) at the step of the post-stream state f: with h = C(f) and
-    f' = S_bc(h) the next post-stream state,
+    4.3 names) in the update that starts from the post-stream state f: with
+    h = C(f) and f' = S_bc(h) the next post-stream state,
       F = sum over links (x, i), x FLUID, x + c_i a WALL cell in `solid`
           (all WALL cells if None), of c_i [h_i(x) + f'_opp(i)(x)],
     the momentum the populations crossing each link hand to the wall."""

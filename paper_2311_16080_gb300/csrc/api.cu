@@ -21,6 +21,7 @@
 
 #include "../../include/xlb.h"
 #include "adjoint.h"
+#include "lattice.cuh"
 #include "launch.h"
 #include "lattice.cuh"
 
@@ -47,6 +48,9 @@ struct xlb_ctx {
   int* fix = nullptr;  // inlet / outlet cells (recomputed after a bulk pass)
   long long n_fix = 0;
   int face[6] = {0, 0, 0, 0, 0, 0};  // described boundary faces (StepParams::face)
+  float* link_q = nullptr;  // Bouzidi wall distance per link (LINK_BZ entries), or null
+  float* inlet_field = nullptr;  // D * N inlet velocities (xlb_set_inlet_profile), or null
+  int inlet_scheme = XLB_INLET_ZOU_HE;
   bool has_inlet_outlet = false;  // INLET, OUTLET or FWALL cells (no adjoint)
   float* init_fields = nullptr;  // (1 + D) * N: rho0, u0 (component-major)
   bool has_init = false;
@@ -78,6 +82,12 @@ struct xlb_ctx {
   int64_t adj_t = -1;  // time index of the adjoint held in abar[acur]
   // kernel variant of the bulk pass (XLB_KERNEL_*)
   int variant = 0;
+  // graph replay of the update (xlb_set_step_graph): g updates per graph, one
+  // executable graph per starting buffer, each valid for one parameter epoch
+  int64_t graph_g = 0;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  uint64_t gexec_epoch[2] = {0, 0};
+  uint64_t epoch = 1;  // bumped by every change of the update's parameters
   // profiling
   bool prof = false;
   std::vector<EventPair> ev_pool;
@@ -102,6 +112,7 @@ static int fail(xlb_ctx* c, int code, const char* fmt, ...) {
 }
 
 static int cuda_fail(xlb_ctx* c, cudaError_t e, const char* what) {
+  cudaGetLastError();  // a failed allocation must not surface again at the next launch check
   return fail(c, e == cudaErrorMemoryAllocation ? XLB_ERR_OOM : XLB_ERR_CUDA, "%s: %s", what,
               cudaGetErrorString(e));
 }
@@ -156,6 +167,8 @@ static StepParams make_params(const xlb_ctx* c) {
     p.inlet_u[2] = 0.f;
   }
   p.eq_rho = c->eq_rho;
+  p.inlet_field = c->inlet_field;
+  p.inlet_regularized = c->inlet_scheme == XLB_INLET_REGULARIZED;
   p.err = c->err_word ? c->err_word + 1 : nullptr;
   p.has_faces = 0;
   for (int f = 0; f < 6; ++f) {
@@ -261,6 +274,7 @@ static int boundary_pass(xlb_ctx* c, const void* fix_src, void* dst) {
   a.src = fix_src ? fix_src : dst;
   a.dst = dst;
   a.links = c->links;
+  a.link_q = c->link_q;
   a.n_links = c->n_links;
   a.fix = c->fix;
   a.n_fix = c->n_fix;
@@ -411,6 +425,15 @@ static void detect_faces(const uint8_t* m, long long nx, long long ny, long long
   for (int f = 0; f < 6; ++f) out[f] = cand[f];
 }
 
+template <int Q>
+static void fill_lattice(int32_t* c, double* w) {
+  for (int i = 0; i < Q; ++i) {
+    if (c)
+      for (int a = 0; a < 3; ++a) c[3 * i + a] = Lattice<Q>::c(i, a);
+    if (w) w[i] = weight_d<Q>(i);
+  }
+}
+
 extern "C" {
 
 const char* xlb_status_string(int s) {
@@ -505,9 +528,13 @@ void xlb_destroy(xlb_ctx* c) {
   xlb_tape_release(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (int k = 0; k < 2; ++k)
+    if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+  for (int k = 0; k < 2; ++k)
     if (c->buf[k]) cudaFree(c->buf[k]);
   if (c->flags) cudaFree(c->flags);
   if (c->links) cudaFree(c->links);
+  if (c->link_q) cudaFree(c->link_q);
+  if (c->inlet_field) cudaFree(c->inlet_field);
   if (c->fix) cudaFree(c->fix);
   if (c->init_fields) cudaFree(c->init_fields);
   if (c->partial) cudaFree(c->partial);
@@ -630,6 +657,8 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
   }
   if (c->flags) cudaFree(c->flags);
   if (c->links) cudaFree(c->links);
+  if (c->link_q) cudaFree(c->link_q);
+  c->link_q = nullptr;  // wall distances belong to the old link table
   if (c->fix) cudaFree(c->fix);
   c->flags = nf;
   c->links = nlinks;
@@ -639,6 +668,130 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
   c->has_inlet_outlet = new_io;
   for (int f = 0; f < 6; ++f) c->face[f] = new_face[f];
   c->has_mask = true;
+  ++c->epoch;
+  return XLB_OK;
+}
+
+int xlb_lattice_table(int lattice, int32_t* c, double* w) {
+  if (lattice == 9)
+    fill_lattice<9>(c, w);
+  else if (lattice == 19)
+    fill_lattice<19>(c, w);
+  else if (lattice == 27)
+    fill_lattice<27>(c, w);
+  else
+    return XLB_ERR_ARG;
+  return XLB_OK;
+}
+
+static int lattice_opposite(int Q, int i) {
+  return Q == 9 ? opposite<9>(i) : (Q == 19 ? opposite<19>(i) : opposite<27>(i));
+}
+
+int xlb_set_inlet_profile(xlb_ctx* c, const float* u) {
+  if (!c) return XLB_ERR_ARG;
+  if (c->tape_open) return fail(c, XLB_ERR_STATE, "boundary values cannot change while a tape is open");
+  const int r = materialize_post_stream(c);  // f_t with the old inlet
+  if (r) return r;
+  if (!u) {
+    if (c->inlet_field) CK(cudaFree(c->inlet_field));
+    c->inlet_field = nullptr;
+    ++c->epoch;
+    return XLB_OK;
+  }
+  const size_t bytes = sizeof(float) * (size_t)c->D * (size_t)c->N;
+  if (!c->inlet_field) CK(cudaMalloc(&c->inlet_field, bytes));
+  CK(cudaMemcpyAsync(c->inlet_field, u, bytes, cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  ++c->epoch;
+  return XLB_OK;
+}
+
+int xlb_set_inlet_scheme(xlb_ctx* c, int scheme) {
+  if (!c) return XLB_ERR_ARG;
+  if (scheme != XLB_INLET_ZOU_HE && scheme != XLB_INLET_REGULARIZED)
+    return fail(c, XLB_ERR_ARG, "unknown inlet scheme %d", scheme);
+  if (c->tape_open) return fail(c, XLB_ERR_STATE, "boundary values cannot change while a tape is open");
+  const int r = materialize_post_stream(c);  // f_t with the old rule
+  if (r) return r;
+  c->inlet_scheme = scheme;
+  ++c->epoch;
+  return XLB_OK;
+}
+
+int xlb_set_wall_distances(xlb_ctx* c, int64_t n, const int64_t* cell, const int32_t* dir, const float* q) {
+  if (!c) return XLB_ERR_ARG;
+  if (n < 0 || (n > 0 && (!cell || !dir || !q))) return fail(c, XLB_ERR_ARG, "n < 0 or a null array");
+  if (!c->has_mask) return fail(c, XLB_ERR_STATE, "set a mask first");
+  if (c->tape_open) return fail(c, XLB_ERR_STATE, "boundary values cannot change while a tape is open");
+  // host copy of the link table; entries of one pulled direction are
+  // contiguous and ascending in the cell index
+  std::vector<int2> hl((size_t)c->n_links);
+  if (c->n_links > 0)
+    CK(cudaMemcpy(hl.data(), c->links, sizeof(int2) * hl.size(), cudaMemcpyDeviceToHost));
+  for (auto& e : hl) e.y &= ~LINK_BZ;
+  std::vector<long long> beg(c->Q + 1, 0);
+  {
+    long long k = 0;
+    for (int j = 0; j <= c->Q; ++j) {
+      while (k < (long long)hl.size() && (hl[k].y & 0xff) < j) ++k;
+      beg[j] = k;
+    }
+  }
+  std::vector<float> hq(hl.size(), 0.f);
+  for (int64_t k = 0; k < n; ++k) {
+    const int i = dir[k];
+    if (i < 1 || i >= c->Q) return fail(c, XLB_ERR_ARG, "link %lld: direction %d out of range", (long long)k, i);
+    if (!(q[k] >= 0.f && q[k] <= 1.f)) return fail(c, XLB_ERR_ARG, "link %lld: q must be in [0, 1]", (long long)k);
+    if (cell[k] < 0 || cell[k] >= c->N) return fail(c, XLB_ERR_ARG, "link %lld: cell out of range", (long long)k);
+    // the link is pulled in the opposite direction j from the wall cell
+    const int j = lattice_opposite(c->Q, i);
+    const int2* lo = hl.data() + beg[j];
+    const int2* hi = hl.data() + beg[j + 1];
+    const int2* e = std::lower_bound(lo, hi, (int)cell[k], [](const int2& a, int v) { return a.x < v; });
+    if (e == hi || e->x != (int)cell[k] || ((e->y >> 8) & 0xff) != XLB_CELL_WALL)
+      return fail(c, XLB_ERR_ARG,
+                  "link %lld (cell %lld, direction %d) is not a ghost link from a FLUID cell to a WALL cell "
+                  "off the boundary faces",
+                  (long long)k, (long long)cell[k], i);
+    const size_t idx = (size_t)(e - hl.data());
+    hl[idx].y |= LINK_BZ;
+    hq[idx] = q[k];
+  }
+  // the new rule acts from the next step on (like xlb_set_bc)
+  int r = materialize_post_stream(c);
+  if (r) return r;
+  if (c->link_q) CK(cudaFree(c->link_q));
+  c->link_q = nullptr;
+  if (n > 0) CK(cudaMalloc(&c->link_q, sizeof(float) * hq.size()));
+  if (n > 0) CK(cudaMemcpy(c->link_q, hq.data(), sizeof(float) * hq.size(), cudaMemcpyHostToDevice));
+  if (!hl.empty()) CK(cudaMemcpy(c->links, hl.data(), sizeof(int2) * hl.size(), cudaMemcpyHostToDevice));
+  ++c->epoch;
+  return XLB_OK;
+}
+
+int xlb_wall_force(xlb_ctx* c, double* out) {
+  if (!c || !out) return XLB_ERR_ARG;
+  if (!c->kind_h) return fail(c, XLB_ERR_STATE, "no post-collision state yet: take a step first");
+  LaunchArgs a = base_args(c);
+  a.src = c->buf[c->cur];
+  a.links = c->links;
+  a.n_links = c->has_mask ? c->n_links : 0;
+  long long b = (a.n_links + 255) / 256;
+  if (b > c->partial_cap) b = c->partial_cap;
+  if (b < 1) b = 1;
+  a.partial_capacity = b;
+  int r = dispatch(c, OP_WALL_FORCE, a);
+  if (r) return r;
+  launch_reduce_final(c->partial, b, c->red_out, c->stream);
+  if (is_device_ptr(out)) {
+    CK(cudaMemcpyAsync(out, c->red_out, 3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    return XLB_OK;
+  }
+  double h[4];
+  CK(cudaMemcpyAsync(h, c->red_out, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 3; ++k) out[k] = h[k];
   return XLB_OK;
 }
 
@@ -668,6 +821,7 @@ int xlb_set_bc(xlb_ctx* c, int type, float rho, const float u[3]) {
     c->eq_rho = rho;
     for (int a = 0; a < 3; ++a) c->eq_u[a] = u[a];
   }
+  ++c->epoch;
   return XLB_OK;
 }
 
@@ -677,6 +831,7 @@ int xlb_set_force(xlb_ctx* c, const float F[3]) {
   if (c->tape_open) return fail(c, XLB_ERR_STATE, "the force cannot change while a tape is open");
   for (int a = 0; a < 3; ++a) c->F[a] = (a < c->D) ? F[a] : 0.f;
   c->has_force = (c->F[0] != 0.f || c->F[1] != 0.f || c->F[2] != 0.f);
+  ++c->epoch;
   return XLB_OK;
 }
 
@@ -718,6 +873,60 @@ static int record_checkpoint(xlb_ctx* c) {
   return XLB_OK;
 }
 
+// Executable graph of graph_g updates starting from buffer `from`, captured
+// on the ctx stream with the current parameters (recaptured when the epoch
+// has moved on).  The graph holds exactly the launches launch_step makes.
+static int step_graph(xlb_ctx* c, int from, cudaGraphExec_t* out) {
+  if (c->gexec[from] && c->gexec_epoch[from] == c->epoch) {
+    *out = c->gexec[from];
+    return XLB_OK;
+  }
+  if (c->gexec[from]) {
+    cudaGraphExecDestroy(c->gexec[from]);
+    c->gexec[from] = nullptr;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(c->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return fail(c, XLB_ERR_STATE, "the ctx stream is already capturing");
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  int cur = from, r = XLB_OK;
+  for (int64_t k = 0; k < c->graph_g && r == XLB_OK; ++k) {
+    r = launch_step(c, c->buf[cur], c->buf[cur ^ 1]);
+    cur ^= 1;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (r != XLB_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return r != XLB_OK ? r : cuda_fail(c, e, "stream capture of the update");
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&c->gexec[from], g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    c->gexec[from] = nullptr;
+    return cuda_fail(c, ei, "cudaGraphInstantiate");
+  }
+  c->gexec_epoch[from] = c->epoch;
+  *out = c->gexec[from];
+  return XLB_OK;
+}
+
+int xlb_set_step_graph(xlb_ctx* c, int64_t steps_per_graph) {
+  if (!c) return XLB_ERR_ARG;
+  if (steps_per_graph < 0 || steps_per_graph > 100000)
+    return fail(c, XLB_ERR_ARG, "steps_per_graph must be in [0, 100000]");
+  if (steps_per_graph != c->graph_g) {
+    for (int k = 0; k < 2; ++k)
+      if (c->gexec[k]) {
+        CK(cudaGraphExecDestroy(c->gexec[k]));
+        c->gexec[k] = nullptr;
+      }
+  }
+  c->graph_g = steps_per_graph;
+  return XLB_OK;
+}
+
 int xlb_step(xlb_ctx* c, int64_t n) {
   if (!c) return XLB_ERR_ARG;
   if (n < 0) return fail(c, XLB_ERR_ARG, "n must be >= 0");
@@ -726,6 +935,16 @@ int xlb_step(xlb_ctx* c, int64_t n) {
     return fail(c, XLB_ERR_STATE, "stepping past the tape length %lld", (long long)c->tape_T);
   for (int64_t k = 0; k < n; ++k) {
     int r;
+    if (c->kind_h && c->graph_g > 0 && !c->tape_open && !c->prof && n - k >= c->graph_g) {
+      cudaGraphExec_t ge = nullptr;
+      r = step_graph(c, c->cur, &ge);
+      if (r) return r;
+      CK(cudaGraphLaunch(ge, c->stream));
+      if (c->graph_g & 1) c->cur ^= 1;
+      c->t += c->graph_g;
+      k += c->graph_g - 1;
+      continue;
+    }
     if (!c->kind_h) {
       r = launch_collide_local(c, c->buf[c->cur]);
       c->kind_h = 1;
@@ -761,6 +980,7 @@ int xlb_set_kernel(xlb_ctx* c, int variant) {
     return fail(c, XLB_ERR_UNSUPPORTED,
                 "the vectorised kernel needs 16-bit storage, D2Q9 or D3Q19, BGK/NONE and nx %% 4 == 0");
   c->variant = variant;
+  ++c->epoch;
   return XLB_OK;
 }
 
@@ -922,6 +1142,8 @@ int xlb_tape_begin(xlb_ctx* c, int64_t n_steps, int64_t k) {
   const int64_t n_ckpt = (n_steps - 1) / k;
   const size_t sb = (state_bytes_raw(c) + 255) / 256 * 256;
   const size_t ab = (sizeof(float) * state_elems(c) + 255) / 256 * 256;
+  if ((uint64_t)(n_ckpt + k) > (SIZE_MAX - 2 * ab) / sb)
+    return fail(c, XLB_ERR_OOM, "a tape of %lld states does not fit in memory", (long long)(n_ckpt + k));
   const size_t need = (size_t)(n_ckpt + k) * sb + 2 * ab;
   if (c->tape_arena_bytes < need) {
     if (c->tape_arena) cudaFree(c->tape_arena);

@@ -99,20 +99,53 @@ __device__ __forceinline__ void write_ghost(S* __restrict__ dst, const StepParam
   Store<S>::st(dst + (long long)i * p.plane + (wx + p.nx * (wy + p.ny * wz)), v);
 }
 
+// Ghost value of a WALL link with a Bouzidi wall distance q (Bouzidi,
+// Firdaouss and Lallemand 2001; the curved-wall rule Section 4.3 names): the
+// value FLUID cell x pulls in direction j, with hi = h_opp(j)(x):
+//   q <  1/2: 2q hi + (1 - 2q) h_opp(j)(x + c_j)  (hi if x + c_j is not FLUID)
+//   q >= 1/2: hi / (2q) + (1 - 1/(2q)) h_j(x)
+// The cells read are FLUID cells of dst, which the boundary pass never writes.
+template <int Q, typename S>
+__device__ __forceinline__ float bouzidi_ghost(const S* __restrict__ dst, const StepParams& p, int x, int j,
+                                               float hi, float q) {
+  int dx = 0, dy = 0, dz = 0, io = 0;
+#pragma unroll
+  for (int jj = 1; jj < Q; ++jj)
+    if (jj == j) {
+      dx = Lattice<Q>::c(jj, 0);
+      dy = Lattice<Q>::c(jj, 1);
+      dz = Lattice<Q>::c(jj, 2);
+      io = opposite<Q>(jj);
+    }
+  if (q < 0.5f) {
+    const int r = x / p.nx;
+    int bx = x - r * p.nx + dx, by = r % p.ny + dy, bz = r / p.ny + dz;
+    bx = bx < 0 ? p.nx - 1 : (bx >= p.nx ? 0 : bx);
+    by = by < 0 ? p.ny - 1 : (by >= p.ny ? 0 : by);
+    bz = bz < 0 ? p.nz - 1 : (bz >= p.nz ? 0 : bz);
+    const int b = bx + p.nx * (by + p.ny * bz);
+    if ((__ldg(p.flags + b) & FLAG_TYPE) != FLUID) return hi;
+    return 2.0f * q * hi + (1.0f - 2.0f * q) * Store<S>::ld_plain(dst + (long long)io * p.plane + b);
+  }
+  const float inv = 0.5f / q;
+  return inv * hi + (1.0f - inv) * Store<S>::ld_plain(dst + (long long)j * p.plane + x);
+}
+
 // Boundary pass on dst, after a pass that wrote post-collision values there.
 // Threads [0, ceil(n_links / 4)) write the ghost values of the links of FLUID
-// cells and of cells on FWALL face planes (4 links each); the next n_fix
-// threads handle one INLET, OUTLET or other FWALL cell each: with
-// `recompute`, its update from src with the full rules (the bulk pass pulled
-// and collided it as if periodic fluid); then the ghosts of its own links.  src is read only by the recomputation, which needs the ghosts of
-// the previous state, already in src.
+// cells and of cells on FWALL face planes (4 links each; LINK_BZ links take
+// the Bouzidi value with link_q[e]); the next n_fix threads handle one INLET,
+// OUTLET or other FWALL cell each: with `recompute`, its update from src with
+// the full rules (the bulk pass pulled and collided it as if periodic fluid);
+// then the ghosts of its own links.  src is read only by the recomputation,
+// which needs the ghosts of the previous state, already in src.
 constexpr int LINKS_PER_THREAD = 4;
 
 template <int Q, typename S, int COLL>
 __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ src, S* __restrict__ dst,
                                                         const StepParams p, const int2* __restrict__ links,
-                                                        int n_links, const int* __restrict__ fix, int n_fix,
-                                                        int recompute) {
+                                                        const float* __restrict__ link_q, int n_links,
+                                                        const int* __restrict__ fix, int n_fix, int recompute) {
   // link threads: LINKS_PER_THREAD links each, strided by the link-thread
   // count so that a warp's loads and stores stay on consecutive entries
   const int n_lt = (n_links + LINKS_PER_THREAD - 1) / LINKS_PER_THREAD;
@@ -128,7 +161,7 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ sr
 #pragma unroll
     for (int m = 0; m < LINKS_PER_THREAD; ++m) {
       h[m] = 0.f;
-      if (l[m].x >= 0 && (l[m].y >> 8) != EQ) {
+      if (l[m].x >= 0 && ((l[m].y >> 8) & 0xff) != EQ) {
         int io = 0;
         const int i = l[m].y & 0xff;
 #pragma unroll
@@ -138,10 +171,14 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ sr
       }
     }
 #pragma unroll
+    for (int m = 0; m < LINKS_PER_THREAD; ++m)
+      if (l[m].x >= 0 && (l[m].y & LINK_BZ))
+        h[m] = bouzidi_ghost<Q, S>(dst, p, l[m].x, l[m].y & 0xff, h[m], __ldg(link_q + k + m * n_lt));
+#pragma unroll
     for (int m = 0; m < LINKS_PER_THREAD; ++m) {
       if (l[m].x < 0) continue;
       const int x = l[m].x, r = x / p.nx;
-      write_ghost<Q, S>(dst, p, x - r * p.nx, r % p.ny, r / p.ny, l[m].y & 0xff, l[m].y >> 8, h[m]);
+      write_ghost<Q, S>(dst, p, x - r * p.nx, r % p.ny, r / p.ny, l[m].y & 0xff, (l[m].y >> 8) & 0xff, h[m]);
     }
     return;
   }
@@ -468,6 +505,65 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_reduce_partial(const S* f, const 
 // ---------------------------------------------------------------------------
 // Dispatch: one function per lattice, switching on storage and collision.
 
+// Momentum-exchange force on the WALL cells of the ghost links (Mei et al.
+// 2002 in the form of Caiazzo and Junk 2008, the method Section 4.3 names)
+// of the update that led to the stored state: f holds h_{t-1} and, in the
+// WALL slots, the ghost values f_j(x, t) pulled at step t.  Each link (FLUID
+// cell x, pulled direction j, WALL source w = x - c_j) hands the wall
+//   c_opp(j) [h_opp(j)(x, t-1) + f_j(x, t)] = -c_j [h_opp(j)(x) + ghost_j(w)],
+// populations taken absolute (stored deviation + w_j on each side).  Grid-
+// stride over the links; one row (F_x, F_y, F_z, 0) of FP64 sums per block.
+template <int Q, typename S>
+__global__ void __launch_bounds__(256) k_wall_force(const S* __restrict__ f, const StepParams p,
+                                                    const int2* __restrict__ links, long long n_links,
+                                                    double* partial) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n_links; e += (long long)gridDim.x * 256) {
+    const int2 l = __ldg(links + e);
+    if (((l.y >> 8) & 0xff) != WALL) continue;
+    const int j = l.y & 0xff;
+    int dx = 0, dy = 0, dz = 0, io = 0;
+    double wj = 0.0;
+#pragma unroll
+    for (int jj = 1; jj < Q; ++jj)
+      if (jj == j) {
+        dx = Lattice<Q>::c(jj, 0);
+        dy = Lattice<Q>::c(jj, 1);
+        dz = Lattice<Q>::c(jj, 2);
+        io = opposite<Q>(jj);
+        wj = weight_d<Q>(jj);
+      }
+    const int x = l.x, r = x / p.nx;
+    int wx = x - r * p.nx - dx, wy = r % p.ny - dy, wz = r / p.ny - dz;
+    wx = wx < 0 ? p.nx - 1 : (wx >= p.nx ? 0 : wx);
+    wy = wy < 0 ? p.ny - 1 : (wy >= p.ny ? 0 : wy);
+    wz = wz < 0 ? p.nz - 1 : (wz >= p.nz ? 0 : wz);
+    const long long w = wx + (long long)p.nx * (wy + (long long)p.ny * wz);
+    const double v = 2.0 * wj + (double)Store<S>::ld_plain(f + (long long)io * p.plane + x) +
+                     (double)Store<S>::ld_plain(f + (long long)j * p.plane + w);
+    acc[0] -= dx * v;
+    acc[1] -= dy * v;
+    acc[2] -= dz * v;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+  __shared__ double red[256 / 32][3];
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) red[threadIdx.x >> 5][k] = acc[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) {
+      double s = 0.0;
+      for (int q = 0; q < 256 / 32; ++q) s += red[q][k];
+      partial[4 * (long long)blockIdx.x + k] = s;
+    }
+    partial[4 * (long long)blockIdx.x + 3] = 0.0;
+  }
+}
+
 // Launches the collision-dependent kernels for collision COLL and, for
 // COLL == COLL_BGK, also the collision-independent ones (init, readouts).
 // One translation unit instantiates this per (Q, storage, collision), so the
@@ -509,8 +605,8 @@ int launch_typed(Op op, const LaunchArgs& a) {
       if (tot <= 0) return 0;
       if (tot > 0x7fffffffLL) return -1;
       const unsigned g = (unsigned)((tot + ROW_BLOCK - 1) / ROW_BLOCK);
-      k_boundary<Q, S, COLL><<<g, ROW_BLOCK, 0, st>>>((const S*)a.src, (S*)a.dst, p, a.links, (int)a.n_links, a.fix,
-                                                     (int)a.n_fix, a.recompute);
+      k_boundary<Q, S, COLL><<<g, ROW_BLOCK, 0, st>>>((const S*)a.src, (S*)a.dst, p, a.links, a.link_q,
+                                                     (int)a.n_links, a.fix, (int)a.n_fix, a.recompute);
       return 0;
     }
     case OP_COLLIDE_LOCAL:
@@ -531,6 +627,14 @@ int launch_typed(Op op, const LaunchArgs& a) {
         if (a.partial_capacity < nblk) return -3;
         k_reduce_partial<Q, S><<<grid, block, 0, st>>>((const S*)a.src, p, a.kind_h, a.partial);
         return 0;
+      case OP_WALL_FORCE: {
+        // blocks: one per 256 links, at most the rows the partial buffer holds
+        long long b = (a.n_links + 255) / 256;
+        if (b > a.partial_capacity) b = a.partial_capacity;
+        if (b < 1) b = 1;
+        k_wall_force<Q, S><<<(unsigned)b, 256, 0, st>>>((const S*)a.src, p, a.links, a.n_links, a.partial);
+        return 0;
+      }
       default:
         break;
     }

@@ -15,7 +15,9 @@ enum Op {
   OP_MACRO = 3,          // rho_out, u_out from src
   OP_REDUCE_PARTIAL = 4, // block partial sums of mass and momentum
   OP_STEP_VEC = 7,       // fused stream + collide, V cells per thread, vector loads
-  OP_BOUNDARY = 8        // ghost values of the boundary links + inlet / outlet recompute
+  OP_BOUNDARY = 8,       // ghost values of the boundary links + fix-up cell recompute
+  OP_WALL_FORCE = 9      // block partial sums of the momentum-exchange force:
+                         // min(ceil(n_links / 256), partial_capacity) rows, at least 1
 };
 
 struct LaunchArgs {
@@ -32,11 +34,12 @@ struct LaunchArgs {
   float* u_out;
   double* partial;
   long long partial_capacity;  // rows of 4 doubles available in partial
-  const int2* links;           // OP_BOUNDARY ghost links {cell, dir | type << 8}
+  const int2* links;           // OP_BOUNDARY / OP_WALL_FORCE ghost links {cell, dir | type << 8 | flags << 16}
+  const float* link_q;         // Bouzidi wall distance of each LINK_BZ link (or null)
   long long n_links;
-  const int* fix;              // OP_BOUNDARY inlet / outlet cells
+  const int* fix;              // OP_BOUNDARY fix-up cells (INLET, OUTLET, FWALL off the faces)
   long long n_fix;
-  int recompute;               // OP_BOUNDARY: recompute the inlet / outlet cells from src
+  int recompute;               // OP_BOUNDARY: recompute the fix-up cells from src
   void* stream;
 };
 
@@ -49,16 +52,16 @@ int launch_d3q27(Op op, const LaunchArgs& a);
 // Number of blocks the row-mapped kernels launch for a lattice (partials).
 long long row_blocks(const StepParams& p);
 
-// Mask preparation: validates codes (< 6), writes flag bytes; err_word is set
+// Mask preparation: validates codes (< 7), writes flag bytes; err_word is set
 // to 1 on an invalid code.  Q picks the stencil used for the FLAG_SLOW test.
 int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int ny, int nz, int* err_word,
                         void* stream);
 int launch_reduce_final(const double* partial, long long n, double* out, void* stream);
 
 // Boundary tables of a mask by compaction: mode 0 selects the FLUID cells
-// whose source in direction `dir` is WALL / LID / EQ (written as links
-// {cell, dir | type << 8}), mode 1 the INLET / OUTLET cells (written to
-// `cells`).  Per block of 256 cells: counts, then ordered writes at the
+// (and FWALL cells of FWALL faces) whose source in direction `dir` is WALL /
+// LID / EQ (written as links {cell, dir | type << 8}), mode 1 the fix-up
+// cells (written to `cells`).  Per block of 256 cells: counts, then ordered writes at the
 // exclusive offsets of the counts.
 long long bnd_list_blocks(long long n);
 // `face` (6 types, or null) lists the described boundary faces: links whose

@@ -43,6 +43,39 @@ __device__ __forceinline__ int src_index(const Nbr& nb, int i) {
   return nb.xo[1 - Lattice<Q>::c(i, 0)] + nb.rb[1 - Lattice<Q>::c(i, 1)][1 - Lattice<Q>::c(i, 2)];
 }
 
+template <int Q>
+__device__ __forceinline__ void moments(const float (&df)[Q], float& drho, float (&j)[3]) {
+  drho = 0.f;
+  j[0] = j[1] = j[2] = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    drho += df[i];
+    if (Lattice<Q>::c(i, 0)) j[0] += Lattice<Q>::c(i, 0) * df[i];
+    if (Lattice<Q>::c(i, 1)) j[1] += Lattice<Q>::c(i, 1) * df[i];
+    if (Lattice<Q>::c(i, 2)) j[2] += Lattice<Q>::c(i, 2) * df[i];
+  }
+}
+
+// Bracket of Eq. 5 without the leading 1: 3 c.u + 4.5 (c.u)^2 - 1.5 u.u
+template <int Q>
+__device__ __forceinline__ float eq_poly(int i, const float (&u)[3], float usq) {
+  float cu = 0.f;
+  if (Lattice<Q>::c(i, 0)) cu += Lattice<Q>::c(i, 0) * u[0];
+  if (Lattice<Q>::c(i, 1)) cu += Lattice<Q>::c(i, 1) * u[1];
+  if (Lattice<Q>::c(i, 2)) cu += Lattice<Q>::c(i, 2) * u[2];
+  return cu * (3.0f + 4.5f * cu) - 1.5f * usq;
+}
+
+// c_i . u
+template <int Q>
+__device__ __forceinline__ float cdot(int i, const float (&u)[3]) {
+  float cu = 0.f;
+  if (Lattice<Q>::c(i, 0)) cu += Lattice<Q>::c(i, 0) * u[0];
+  if (Lattice<Q>::c(i, 1)) cu += Lattice<Q>::c(i, 1) * u[1];
+  if (Lattice<Q>::c(i, 2)) cu += Lattice<Q>::c(i, 2) * u[2];
+  return cu;
+}
+
 // Pull: df_i(x) = h_i(x - c_i), periodic (Eq. 2).  Sources on a boundary face
 // (StepParams::face) take the rule instead, chosen before any load so that
 // each direction is still exactly one load:
@@ -144,22 +177,87 @@ __device__ __forceinline__ void pull_periodic(const S* __restrict__ src, const S
 //   rho = [sum_{c_x=0} f_i + 2 sum_{c_x=-1} f_i] / (1 - u_x),
 //   f_i = f_opp(i) + f_i^eq - f_opp(i)^eq = f_opp(i) + 6 w_i rho (c_i . u).
 // In deviations the rest parts of the numerator sum to exactly 1.
+// The inlet velocity is StepParams::inlet_u, or the cell's entry of
+// StepParams::inlet_field (a velocity profile) when that is set.
 template <int Q>
-__device__ __forceinline__ void zou_he_inlet(const StepParams& p, float (&df)[Q]) {
+__device__ __forceinline__ void inlet_velocity(const StepParams& p, int self, float (&u)[3]) {
+  u[0] = p.inlet_u[0];
+  u[1] = p.inlet_u[1];
+  u[2] = p.inlet_u[2];
+  if (p.inlet_field) {
+    const long long n = (long long)p.nx * p.ny * p.nz;
+    u[0] = p.inlet_field[self];
+    u[1] = p.inlet_field[n + self];
+    u[2] = Lattice<Q>::D == 3 ? p.inlet_field[2 * n + self] : 0.f;
+  }
+}
+
+template <int Q>
+__device__ __forceinline__ void zou_he_inlet(const StepParams& p, int self, float (&df)[Q]) {
+  float u[3];
+  inlet_velocity<Q>(p, self, u);
   float s = 1.0f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (Lattice<Q>::c(i, 0) == 0) s += df[i];
     if (Lattice<Q>::c(i, 0) == -1) s += 2.0f * df[i];
   }
-  const float rho = s / (1.0f - p.inlet_u[0]);
+  const float rho = s / (1.0f - u[0]);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (Lattice<Q>::c(i, 0) == 1) {
-      float cu = Lattice<Q>::c(i, 0) * p.inlet_u[0] + Lattice<Q>::c(i, 1) * p.inlet_u[1];
-      if (Lattice<Q>::D == 3) cu += Lattice<Q>::c(i, 2) * p.inlet_u[2];
+      float cu = Lattice<Q>::c(i, 0) * u[0] + Lattice<Q>::c(i, 1) * u[1];
+      if (Lattice<Q>::D == 3) cu += Lattice<Q>::c(i, 2) * u[2];
       df[i] = df[opposite<Q>(i)] + 6.0f * weight<Q>(i) * rho * cu;
     }
+  }
+}
+
+// Regularized velocity inlet (Latt et al. 2008, the other inflow rule
+// Section 4.3 names): rho as for Zou-He; non-equilibrium parts of the known
+// populations, those of the unknown (c_x = +1) ones by bounce-back;
+// Pi = sum_i c_i c_i f^neq_i; every population becomes
+//   f_i = f_i^eq(rho, u) + w_i / (2 cs^4) (c_i c_i - cs^2 I) : Pi.
+template <int Q>
+__device__ __forceinline__ void regularized_inlet(const StepParams& p, int self, float (&df)[Q]) {
+  float u[3];
+  inlet_velocity<Q>(p, self, u);
+  float s = 1.0f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (Lattice<Q>::c(i, 0) == 0) s += df[i];
+    if (Lattice<Q>::c(i, 0) == -1) s += 2.0f * df[i];
+  }
+  const float rho = s / (1.0f - u[0]);
+  const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  // equilibrium deviations f_i^eq - w_i, then the non-equilibrium parts
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float eqd = weight<Q>(i) * (rho - 1.0f) + weight<Q>(i) * rho * eq_poly<Q>(i, u, usq);
+    df[i] -= eqd;  // df now holds f^neq_i
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    if (Lattice<Q>::c(i, 0) == 1) df[i] = df[opposite<Q>(i)];
+  float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float cx = Lattice<Q>::c(i, 0), cy = Lattice<Q>::c(i, 1), cz = Lattice<Q>::c(i, 2);
+    pxx += cx * cx * df[i];
+    pyy += cy * cy * df[i];
+    pzz += cz * cz * df[i];
+    pxy += cx * cy * df[i];
+    pxz += cx * cz * df[i];
+    pyz += cy * cz * df[i];
+  }
+  constexpr float cs2 = 1.0f / 3.0f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float cx = Lattice<Q>::c(i, 0), cy = Lattice<Q>::c(i, 1), cz = Lattice<Q>::c(i, 2);
+    float qpi = (cx * cx - cs2) * pxx + (cy * cy - cs2) * pyy + 2.0f * cx * cy * pxy;
+    if (Lattice<Q>::D == 3) qpi += (cz * cz - cs2) * pzz + 2.0f * (cx * cz * pxz + cy * cz * pyz);
+    const float eqd = weight<Q>(i) * (rho - 1.0f) + weight<Q>(i) * rho * eq_poly<Q>(i, u, usq);
+    df[i] = eqd + 4.5f * weight<Q>(i) * qpi;  // 1 / (2 cs^4) = 4.5
   }
 }
 
@@ -174,7 +272,12 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ src, const StepP
                                           int type, const Nbr& nb, float (&df)[Q]) {
   const int self = x + p.nx * (y + p.ny * z);
   pull_periodic<Q, S>(src, p, nb, self, x, y, z, df);
-  if (type == INLET) zou_he_inlet<Q>(p, df);
+  if (type == INLET) {
+    if (p.inlet_regularized)
+      regularized_inlet<Q>(p, self, df);
+    else
+      zou_he_inlet<Q>(p, self, df);
+  }
   if (type == OUTLET) {
     const int xl = wrap_m(x, p.nx);
     Nbr nl;
@@ -185,39 +288,6 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ src, const StepP
     for (int i = 0; i < Q; ++i)
       if (Lattice<Q>::c(i, 0) == -1) df[i] = dl[i];
   }
-}
-
-template <int Q>
-__device__ __forceinline__ void moments(const float (&df)[Q], float& drho, float (&j)[3]) {
-  drho = 0.f;
-  j[0] = j[1] = j[2] = 0.f;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    drho += df[i];
-    if (Lattice<Q>::c(i, 0)) j[0] += Lattice<Q>::c(i, 0) * df[i];
-    if (Lattice<Q>::c(i, 1)) j[1] += Lattice<Q>::c(i, 1) * df[i];
-    if (Lattice<Q>::c(i, 2)) j[2] += Lattice<Q>::c(i, 2) * df[i];
-  }
-}
-
-// Bracket of Eq. 5 without the leading 1: 3 c.u + 4.5 (c.u)^2 - 1.5 u.u
-template <int Q>
-__device__ __forceinline__ float eq_poly(int i, const float (&u)[3], float usq) {
-  float cu = 0.f;
-  if (Lattice<Q>::c(i, 0)) cu += Lattice<Q>::c(i, 0) * u[0];
-  if (Lattice<Q>::c(i, 1)) cu += Lattice<Q>::c(i, 1) * u[1];
-  if (Lattice<Q>::c(i, 2)) cu += Lattice<Q>::c(i, 2) * u[2];
-  return cu * (3.0f + 4.5f * cu) - 1.5f * usq;
-}
-
-// c_i . u
-template <int Q>
-__device__ __forceinline__ float cdot(int i, const float (&u)[3]) {
-  float cu = 0.f;
-  if (Lattice<Q>::c(i, 0)) cu += Lattice<Q>::c(i, 0) * u[0];
-  if (Lattice<Q>::c(i, 1)) cu += Lattice<Q>::c(i, 1) * u[1];
-  if (Lattice<Q>::c(i, 2)) cu += Lattice<Q>::c(i, 2) * u[2];
-  return cu;
 }
 
 // The collision code below walks the rest direction and the pairs

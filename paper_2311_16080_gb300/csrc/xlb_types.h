@@ -43,6 +43,8 @@ struct StepParams {
   float eq_df[27];       // f_i^eq(rho_eq, u_eq) - w_i (equilibrium-BC cells)
   float eq_rho, eq_u[3];
   float inlet_u[3];      // Zou-He inlet velocity
+  const float* inlet_field;  // or per-cell inlet velocities (D x N, component-major), or null
+  int inlet_regularized;     // INLET rule: 0 Zou-He, 1 regularized
   int* err;              // device error word for kernels with bounded waits
   // Boundary faces: type (0 = none, WALL, LID, EQ or FWALL) of each whole
   // face plane x = 0, x = nx-1, y = 0, y = ny-1, z = 0, z = nz-1 that the
@@ -53,6 +55,10 @@ struct StepParams {
   int face[6];
   int has_faces;
 };
+
+// Ghost link entries are int2 {cell, dir | type << 8 | flags << 16}; LINK_BZ
+// marks a WALL link with a Bouzidi wall distance (in a parallel float array).
+constexpr int LINK_BZ = 1 << 16;
 
 // Device error codes written to StepParams::err.
 constexpr int DEVERR_TIMEOUT = 1;

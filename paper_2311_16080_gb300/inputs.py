@@ -115,7 +115,7 @@ def schafer_turek_2d(n_d, u_mean):
 
 def ball_links(mask, center, radius, c):
     """Links from FLUID cells to the cells of a disc / ball (cell centres
-    within `radius` of `center` = (x, y[, z])), with the fraction q in (0, 1]
+    within `radius` of `center` = (x, y[, z])), with the fraction q in [0, 1]
     of each link at which it enters the circle / sphere.  c: the lattice
     velocities (Q x d, Figure 1 order).  Returns (cells as flat indices, x
     fastest; directions; q)."""
@@ -140,7 +140,8 @@ def ball_links(mask, center, radius, c):
         a = float(ci @ ci)
         b = 2.0 * (r0 @ ci)
         cc = (r0 * r0).sum(axis=1) - radius * radius
-        t = (-b - np.sqrt(b * b - 4.0 * a * cc)) / (2.0 * a)
+        t = (-b - np.sqrt(np.maximum(b * b - 4.0 * a * cc, 0.0))) / (2.0 * a)
+        t = np.clip(t, 0.0, 1.0)   # a cell centre on the surface gives q = 0 up to rounding
         cells.append(np.ravel_multi_index(tuple(src.T), mask.shape))
         dirs.append(np.full(len(src), i))
         qs.append(t)

@@ -26,6 +26,7 @@ XLB_COLL_NONE, XLB_COLL_BGK, XLB_COLL_KBC = 0, 1, 2
 XLB_STORE_F32, XLB_STORE_F16, XLB_STORE_BF16 = 0, 1, 2
 XLB_KERNEL_AUTO, XLB_KERNEL_DIRECT, XLB_KERNEL_VEC = 0, 1, 2
 XLB_CELL_FLUID, XLB_CELL_WALL, XLB_CELL_LID, XLB_CELL_INLET, XLB_CELL_OUTLET, XLB_CELL_EQ, XLB_CELL_FWALL = range(7)
+XLB_INLET_ZOU_HE, XLB_INLET_REGULARIZED = 0, 1
 
 STORAGE = {"f32": XLB_STORE_F32, "f16": XLB_STORE_F16, "bf16": XLB_STORE_BF16}
 COLLISION = {"none": XLB_COLL_NONE, "bgk": XLB_COLL_BGK, "kbc": XLB_COLL_KBC}
@@ -46,6 +47,7 @@ _PROTOS = {
     "xlb_last_error": (C.c_char_p, [_vp]),
     "xlb_status_string": (C.c_char_p, [_i]),
     "xlb_omega_from_nu": (_d, [_d]),
+    "xlb_lattice_table": (_i, [_i, _vp, _vp]),
     "xlb_set_mask": (_i, [_vp, _vp]),
     "xlb_set_bc": (_i, [_vp, _i, _f, C.POINTER(_f)]),
     "xlb_boundary_links": (_i, [_vp, C.POINTER(_i64), C.POINTER(_i64)]),
@@ -68,6 +70,11 @@ _PROTOS = {
     "xlb_tape_end": (_i, [_vp]),
     "xlb_tape_release": (_i, [_vp]),
     "xlb_set_kernel": (_i, [_vp, _i]),
+    "xlb_set_step_graph": (_i, [_vp, _i64]),
+    "xlb_set_inlet_profile": (_i, [_vp, _vp]),
+    "xlb_set_inlet_scheme": (_i, [_vp, _i]),
+    "xlb_set_wall_distances": (_i, [_vp, _i64, _vp, _vp, _vp]),
+    "xlb_wall_force": (_i, [_vp, _vp]),
     "xlb_get_kernel": (_i, [_vp, C.POINTER(_i)]),
     "xlb_batch_create": (_i, [C.POINTER(_vp), _i, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _d, _i, _vp]),
     "xlb_batch_destroy": (None, [_vp]),
@@ -280,6 +287,56 @@ def xlb_set_kernel(ctx, variant=XLB_KERNEL_AUTO):
     _check(load().xlb_set_kernel(ctx, int(variant)), ctx)
 
 
+def xlb_lattice_table(lattice):
+    """(c[Q, 3] int32, w[Q] float64): the library's velocity set and weights."""
+    q = int(lattice)
+    c = np.zeros((q, 3), np.int32)
+    w = np.zeros(q, np.float64)
+    _check(load().xlb_lattice_table(q, c.ctypes.data, w.ctypes.data))
+    return c, w
+
+
+def xlb_set_step_graph(ctx, steps_per_graph):
+    _check(load().xlb_set_step_graph(ctx, int(steps_per_graph)), ctx)
+
+
+def xlb_set_inlet_profile(ctx, u):
+    """u: D*N float32 (numpy, torch tensor or raw pointer), or None."""
+    if isinstance(u, np.ndarray):
+        u = np.ascontiguousarray(u, dtype=np.float32)
+    _check(load().xlb_set_inlet_profile(ctx, _ptr(u)), ctx)
+
+
+def xlb_set_inlet_scheme(ctx, scheme):
+    v = {"zou_he": XLB_INLET_ZOU_HE, "regularized": XLB_INLET_REGULARIZED}.get(scheme, scheme)
+    _check(load().xlb_set_inlet_scheme(ctx, int(v)), ctx)
+
+
+def xlb_set_wall_distances(ctx, cells, dirs, q):
+    """Bouzidi wall distances of links (cell, direction toward the WALL
+    neighbour, q in [0, 1]); host arrays."""
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    dirs = np.ascontiguousarray(dirs, dtype=np.int32)
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    if not (cells.shape == dirs.shape == q.shape and cells.ndim == 1):
+        raise ValueError("cells, dirs and q must be 1-D arrays of one length")
+    _check(load().xlb_set_wall_distances(ctx, cells.size, cells.ctypes.data, dirs.ctypes.data,
+                                         q.ctypes.data), ctx)
+
+
+def xlb_wall_force(ctx, out=None):
+    """Momentum-exchange force on the WALL cells (3 doubles).  With `out`
+    (a device pointer or a torch CUDA tensor view) the result is written
+    there asynchronously; otherwise it is returned as a numpy array."""
+    if out is not None:
+        p = out if isinstance(out, int) else out.data_ptr()
+        _check(load().xlb_wall_force(ctx, C.c_void_p(p)), ctx)
+        return None
+    h = np.zeros(3, np.float64)
+    _check(load().xlb_wall_force(ctx, h.ctypes.data), ctx)
+    return h
+
+
 def xlb_get_kernel(ctx):
     v = C.c_int()
     _check(load().xlb_get_kernel(ctx, C.byref(v)), ctx)
@@ -398,6 +455,21 @@ class Simulation:
 
     def kernel(self):
         return xlb_get_kernel(self.ctx)
+
+    def set_step_graph(self, steps_per_graph):
+        xlb_set_step_graph(self.ctx, steps_per_graph)
+
+    def set_inlet_profile(self, u):
+        xlb_set_inlet_profile(self.ctx, u)
+
+    def set_inlet_scheme(self, scheme):
+        xlb_set_inlet_scheme(self.ctx, scheme)
+
+    def set_wall_distances(self, cells, dirs, q):
+        xlb_set_wall_distances(self.ctx, cells, dirs, q)
+
+    def wall_force(self, out=None):
+        return xlb_wall_force(self.ctx, out)
 
     def init(self, rho=None, u=None):
         xlb_init(self.ctx, rho, u)

@@ -57,3 +57,31 @@ def test_status_strings_and_host_helpers(lib):
     # Eq. 4 with dt = 1: omega = 1 / (3 nu + 1/2)
     assert abs(X.xlb_omega_from_nu(0.1) - 1.25) < 1e-15
     X.xlb_destroy(None)
+
+
+def test_lattice_table_matches_figure_1(lib):
+    """The library's direction order (host call, no GPU) is Figure 1's, with
+    the standard weights; it is the order xlb_set_wall_distances expects."""
+    import os
+    from paper_2311_16080_gb300 import xlb as X
+    gold, cur = {}, None
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "lattice_velocities.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("["):
+            cur = line.strip("[]")
+            gold[cur] = []
+        else:
+            gold[cur].append(tuple(int(v) for v in line.split()))
+    wsets = {9: {0: 4 / 9, 1: 1 / 9, 2: 1 / 36}, 19: {0: 1 / 3, 1: 1 / 18, 2: 1 / 36},
+             27: {0: 8 / 27, 1: 2 / 27, 2: 1 / 54, 3: 1 / 216}}
+    for q in (9, 19, 27):
+        c, w = X.xlb_lattice_table(q)
+        g = gold[f"D{2 if q == 9 else 3}Q{q}"]
+        d = len(g[0])
+        g = [(0,) * d] + g          # the rest velocity comes first
+        assert [tuple(int(v) for v in row[:d]) for row in c] == g
+        assert all(abs(w[i] - wsets[q][int((c[i] ** 2).sum())]) < 1e-16 for i in range(q))
+    with pytest.raises(X.XlbError):
+        X.xlb_lattice_table(15)

@@ -90,13 +90,13 @@ def test_checkpoint_interval_does_not_change_gradient():
 def test_adjoint_matches_central_differences():
     """The gradient of the kinetic energy in the central box with respect to
     the initial density, dotted with random directions, against FP64 central
-    differences of the oracle (eps = 1e-6)."""
+    differences of the oracle (eps = 1e-6), 16 directions."""
     c = _case(19, (16, 16, 16), False, None, seed=5)
     steps = 40
     g_rho, _ = gpu_gradient(c, steps, k=10)
     rng = np.random.default_rng(77)
     eps = 1e-6
-    for _ in range(4):
+    for _ in range(16):
         d = rng.standard_normal(c.shape)
         fd = (oracle_loss(c, c.rho0 + eps * d, steps) - oracle_loss(c, c.rho0 - eps * d, steps)) / (2 * eps)
         assert abs(float((g_rho * d).sum()) - fd) <= 1e-3 * abs(fd)
