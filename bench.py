@@ -151,8 +151,9 @@ def run_ours(args, rank, world, dist):
     sim, mask = _cavity_sim(torch, X, I, n, args.storage, stream.cuda_stream)
     if args.kernel != "auto":
         sim.set_kernel(args.kernel)
-    kname = ("k_sc_vec<19,float,BGK,4> (4 cells per thread)" if sim.kernel() == X.XLB_KERNEL_VEC
-             else "k_stream_collide<19,float,BGK> (one cell per thread)")
+    st_name = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16"}[args.storage]
+    kname = (f"k_sc_vec<19,{st_name},BGK,4> (4 cells per thread)" if sim.kernel() == X.XLB_KERNEL_VEC
+             else f"k_stream_collide<19,{st_name},BGK> (one cell per thread)")
     fluid = int((mask == 0).sum())
     n_links, n_fix = X.xlb_boundary_links(sim.ctx)
     split = n_links + n_fix > 0
