@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, S, COLL>::value)
   Nbr nb;
   make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
   float df[Q];
-  pull_periodic<Q, S, FW>(src, p, nb, c.self, c.x, c.y, c.z, df);
-  if (FW && COLL != COLL_NONE && on_fwall_face(p, c.x, c.y, c.z))
+  const bool on_fwall = pull_periodic<Q, S, FW>(src, p, nb, c.self, c.x, c.y, c.z, df);
+  if (FW && COLL != COLL_NONE && on_fwall)
     reverse_populations<Q>(df);
   else
     collide<Q, COLL>(df, p);

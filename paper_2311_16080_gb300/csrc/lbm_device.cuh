@@ -100,16 +100,6 @@ __device__ __forceinline__ int face_combine(int a, int b, int c) {
   return a | b | c;
 }
 
-// Does cell (x, y, z) lie on an FWALL face plane?
-// Such a cell reverses its populations instead of colliding.  Where a WALL
-// face meets the plane the cell is WALL and its slots are never read, so
-// reversing it there too is harmless.
-__device__ __forceinline__ bool on_fwall_face(const StepParams& p, int x, int y, int z) {
-  return (p.face[0] == FWALL && x == 0) || (p.face[1] == FWALL && x == p.nx - 1) ||
-         (p.face[2] == FWALL && y == 0) || (p.face[3] == FWALL && y == p.ny - 1) ||
-         (p.face[4] == FWALL && z == 0) || (p.face[5] == FWALL && z == p.nz - 1);
-}
-
 // Full-way bounce-back (Section 3.5): the collision of an FWALL cell sends
 // every population back where it came from, f*_i = f_opp(i).
 template <int Q>
@@ -123,8 +113,11 @@ __device__ __forceinline__ void reverse_populations(float (&df)[Q]) {
     }
 }
 
+// Returns, with FW, whether the cell itself lies on an FWALL face plane (its
+// own coordinates then count as near a face, so that only warps holding such
+// cells evaluate it).
 template <int Q, typename S, bool FW = true>
-__device__ __forceinline__ void pull_periodic(const S* __restrict__ src, const StepParams& p, const Nbr& nb,
+__device__ __forceinline__ bool pull_periodic(const S* __restrict__ src, const StepParams& p, const Nbr& nb,
                                               int self, int x, int y, int z, float (&df)[Q]) {
   int fcx[3] = {0, 0, 0}, fcy[3] = {0, 0, 0}, fcz[3] = {0, 0, 0};
   bool near = false;
@@ -138,7 +131,7 @@ __device__ __forceinline__ void pull_periodic(const S* __restrict__ src, const S
       fcx[k] = (cx & 1 ? p.face[0] : 0) | (cx & 2 ? p.face[1] : 0);
       fcy[k] = (cy & 1 ? p.face[2] : 0) | (cy & 2 ? p.face[3] : 0);
       fcz[k] = p.nz > 1 ? ((cz & 1 ? p.face[4] : 0) | (cz & 2 ? p.face[5] : 0)) : 0;
-      near |= (k != 1) && (fcx[k] | fcy[k] | fcz[k]);
+      near |= (k != 1 || FW) && (fcx[k] | fcy[k] | fcz[k]);
     }
   }
   const S* base = src;
@@ -151,7 +144,7 @@ __device__ __forceinline__ void pull_periodic(const S* __restrict__ src, const S
       df[i] = Store<S>::ld(base + src_index<Q>(nb, i));
       base += p.plane;
     }
-    return;
+    return false;
   }
   // all loads first (addresses chosen branch-free), adjustments after, so
   // the Q loads stay in flight together
@@ -171,6 +164,9 @@ __device__ __forceinline__ void pull_periodic(const S* __restrict__ src, const S
     if (t == EQ) df[i] = p.eq_df[i];
     if (t == LID) df[i] += p.lid_term[i];
   }
+  // where a WALL face meets an FWALL plane the cell is WALL and its slots are
+  // never read, so reversing it as well is harmless
+  return FW && (fcx[1] == FWALL || fcy[1] == FWALL || fcz[1] == FWALL);
 }
 
 // Zou-He velocity inlet (inflow along +x; unknown populations have c_x = +1):
