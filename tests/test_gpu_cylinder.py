@@ -88,10 +88,12 @@ def test_cylinder_parity_fp16():
     assert rel_l2(ug[:, fl], uo[:, fl]) <= 5e-3
 
 
-def test_sphere_bouzidi_d3q19():
+@pytest.mark.parametrize("q,coll,inlet", [(19, "bgk", "zou_he"), (19, "bgk", "regularized"),
+                                          (27, "kbc", "regularized")])
+def test_sphere_bouzidi_3d(q, coll, inlet):
     """A sphere of radius 3.27 between an INLET and an OUTLET plane, periodic
     in y and z, constant inflow, Bouzidi links on the sphere."""
-    lat = O.Lattice(19)
+    lat = O.Lattice(q)
     nx, ny, nz = 40, 16, 14
     center, radius = (12.3, 7.6, 6.8), 3.27
     m = np.zeros((nz, ny, nx), np.uint8)
@@ -100,22 +102,23 @@ def test_sphere_bouzidi_d3q19():
     m[ball] = O.WALL
     m[:, :, 0] = O.INLET
     m[:, :, -1] = O.OUTLET
-    cells, dirs, q = I.ball_links(m, center, radius, lat.c)
-    q = q.astype(np.float32)
-    wq = np.full((19,) + m.shape, np.nan)
-    wq[(dirs,) + np.unravel_index(cells, m.shape)] = q
+    cells, dirs, qd = I.ball_links(m, center, radius, lat.c)
+    qd = qd.astype(np.float32)
+    wq = np.full((lat.q,) + m.shape, np.nan)
+    wq[(dirs,) + np.unravel_index(cells, m.shape)] = qd
     uin = (0.04, 0.0, 0.0)
-    p = O.Params(lat, 1.6, bc=O.BC(3, inlet_u=uin, wall_q=wq))
+    p = O.Params(lat, 1.6, collision=coll, bc=O.BC(3, inlet_u=uin, wall_q=wq, inlet_scheme=inlet))
     u0 = np.zeros((3,) + m.shape)
     u0[0][O.fluid_like(m)] = uin[0]
     f = O.run(lat, O.init_state(lat, np.ones(m.shape), u0, m, p), m, p, 149)
     Fo = O.wall_force(lat, f, m, p)          # the update 149 -> 150
     f = O.step(lat, f, m, p)
     _, uo = O.macroscopic(lat, f, m, p)
-    s = X.Simulation(19, (nx, ny, nz), 1.6, "bgk", "f32")
+    s = X.Simulation(q, (nx, ny, nz), 1.6, coll, "f32")
     s.set_mask(m)
     s.set_bc(X.XLB_CELL_INLET, 1.0, uin)
-    s.set_wall_distances(cells, dirs, q)
+    s.set_inlet_scheme(inlet)
+    s.set_wall_distances(cells, dirs, qd)
     s.init(np.ones(m.shape, np.float32), u0.astype(np.float32))
     s.step(150)
     _, ug = s.macroscopic()
