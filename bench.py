@@ -490,6 +490,8 @@ def schafer_turek(torch, X, I, stream, n_d=80, u=0.003, re=100.0, t_end=100.0, e
     cd = 2.0 * Fh[:, 0] / (u * u * n_d)
     cl = 2.0 * Fh[:, 1] / (u * u * n_d)
     win = t >= 50.0
+    if not win.any():  # a short run (profiling): timing only
+        return {"schafer_turek_steps": steps, "schafer_turek_s": round(ms / 1e3, 3)}
     x = cl[win] - cl[win].mean()
     tw = t[win]
     k = np.flatnonzero((x[:-1] < 0) & (x[1:] >= 0))
@@ -586,14 +588,20 @@ def run_reference(args, rank, world):
 
 def run_profile_case(args):
     """One secondary workload's loop only, for a profiler: the adjoint on a
-    128^3 periodic D3Q19 lattice (60 steps, checkpoints every 20), or the KBC
-    D3Q27 sphere channel at 256 x 128 x 128 (args.steps steps)."""
+    128^3 periodic D3Q19 lattice (60 steps, checkpoints every 20), the KBC
+    D3Q27 sphere channel at 256 x 128 x 128 (args.steps steps), or the
+    Section 4.3 cylinder at full resolution (100 * args.steps steps, graph
+    replay, the wall force every 100 steps)."""
     import torch
     from paper_2311_16080_gb300 import inputs as I
     from paper_2311_16080_gb300 import xlb as X
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     t0 = time.perf_counter()
+    if args.profile_case == "cylinder":
+        r = schafer_turek(torch, X, I, stream, t_end=100 * args.steps * 0.003 / 80)
+        print(json.dumps({"profile_case": "cylinder", **r, "seconds": round(time.perf_counter() - t0, 3)}))
+        return
     if args.profile_case == "adjoint":
         m, T = 128, 60
         rho0 = torch.from_numpy((1.0 + I.density_perturbation((m, m, m), 1e-3, seed=1234)).astype(np.float32)).cuda()
@@ -628,7 +636,7 @@ def main():
     ap.add_argument("--kernel", choices=["auto", "direct", "vec"], default="auto")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage (default f32, the benchmark workload; others for profiling)")
-    ap.add_argument("--profile-case", choices=["adjoint", "kbc"], default=None,
+    ap.add_argument("--profile-case", choices=["adjoint", "kbc", "cylinder"], default=None,
                     help="run only one secondary workload's loop (for profilers); prints no bench line")
     ap.add_argument("--size", type=int, default=N_CAV,
                     help="cavity edge (default 256, the benchmark workload; smaller only for profiling)")
