@@ -27,7 +27,7 @@ Array convention: populations are ``f[i, z, y, x]`` in 3D and ``f[i, y, x]`` in
 a = x, y, z.  All functions accept real or complex arrays so that complex-step
 derivatives can pin the adjoint.
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
 
 * weights w_i are not printed (Section 2 only names them); the standard
   D2Q9 / D3Q19 / D3Q27 weights are used, pinned by the lattice isotropy
@@ -43,8 +43,7 @@ Readings of points the paper leaves open (each also listed in the design doc):
 * INLET cells apply Zou-He velocity reconstruction for the populations with
   c_x = +1 (non-equilibrium bounce-back of every unknown, no transverse term);
 * OUTLET cells copy their c_x = -1 populations from the cell at x-1
-  (zero-gradient extrapolation) -- parity unpinned: nothing but its own
-  definition checks this rule;
+  (zero-gradient extrapolation);
 * observables are those of the post-stream state f_t; the reported velocity
   with a body force is (j + F/2) / rho;
 * solid (WALL, LID) cells report rho = 0, u = 0;
@@ -394,10 +393,12 @@ def regularized_inlet(lat: Lattice, f, mask, bc: BC):
 
 
 def outflow(lat: Lattice, f_plain, f, mask):
-    """Zero-gradient outflow on OUTLET cells: populations with c_x = -1 take
-    the value that the pull rule gives at the cell x - 1.  Parity unpinned:
-    the paper only cites an extrapolation scheme, so no closed form or
-    printed value checks this reading."""
+    """Zero-gradient outflow on OUTLET cells (Section 4.3 cites an
+    extrapolation outflow): populations with c_x = -1 take the value that the
+    pull rule gives at the cell x - 1.  The unknown populations entering at
+    the outlet are thereby the outlet plane's own post-collision c_x = -1
+    populations, moved transversally, so the mass lost per step equals the
+    plane's x-momentum, and a flow uniform in x passes unchanged."""
     sel = mask == OUTLET
     if not sel.any():
         return f
