@@ -31,6 +31,7 @@ N_CAV = 256
 LID_U = 0.05
 RE = 1000.0
 BYTES_PER_CELL_F32 = 2 * 19 * 4   # one read + one write of 19 FP32 populations
+REPEATS = 5                       # timed regions per run; the median is reported
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -163,18 +164,23 @@ def run_ours(args, rank, world, dist):
     # warm-up (also takes the one local collision after initialisation)
     sim.step(args.warmup)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the timed region (exactly K steps, barrier + synchronize on both sides)
+    # is taken REPEATS times; the median run gives the value
+    runs = []
     with ClockSampler(dev) as clk:
-        torch.cuda.synchronize()
-        e0.record(stream)
-        sim.step(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms_max = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+        for _ in range(REPEATS):
+            if dist:
+                dist.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sim.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            runs.append(max_over_ranks(e0.elapsed_time(e1), dist, "cuda"))
+    ms_max = float(np.median(runs))
     mass, _ = sim.reduce()  # FP64 conservation check on every benchmark run
     ms_step = ms_max / args.steps
     mlups = job_mlups(cells, args.steps, world, ms_max)
@@ -192,19 +198,29 @@ def run_ours(args, rank, world, dist):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sim2.set_mask(h_mask)
+    t1 = time.perf_counter()
     sim2.init(h_rho, h_u)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
     sim2.step(args.steps)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
     X.xlb_macroscopic(sim2.ctx, o_rho, o_u)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    t4 = time.perf_counter()
+    e2e_s = t4 - t0
     sim2.close()
     e2e = {"value": world * cells * args.steps / (e2e_s * 1e6), "unit": "MLUPS",
            "h2d_bytes_per_step": (h_mask.numel() + 4 * (h_rho.numel() + h_u.numel())) / args.steps,
-           "d2h_bytes_per_step": 4 * (o_rho.numel() + o_u.numel()) / args.steps}
+           "d2h_bytes_per_step": 4 * (o_rho.numel() + o_u.numel()) / args.steps,
+           "phases_ms": {"set_mask": round(1e3 * (t1 - t0), 3), "init_upload": round(1e3 * (t2 - t1), 3),
+                         "steps": round(1e3 * (t3 - t2), 3), "readback": round(1e3 * (t4 - t3), 3)}}
 
     peak, peak_kind = hbm_peak()
     esz = 4 if args.storage == "f32" else 2
-    algo_bytes = 2 * 19 * esz * fluid + cells  # populations of fluid cells + the mask byte
+    # one read and one write of every population of every cell per update
+    # (the paper's MLUPS counts all cells; the bulk pass updates all of them)
+    algo_bytes = 2 * 19 * esz * cells
     achieved = algo_bytes / (ms_step * 1e-3) / 1e9
     if achieved > 1.15 * peak:
         raise RuntimeError(f"timed kernel exceeds the measured copy bandwidth ({achieved:.0f} GB/s): "
@@ -213,13 +229,16 @@ def run_ours(args, rank, world, dist):
             "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
             "kernel": kname,
             "algorithmic_bytes_per_launch": algo_bytes,
+            "bytes_per_cell": 2 * 19 * esz,
             "frac_of_8TBs_nominal": round(achieved / 8000.0, 4)}
-    prof_traffic = _profile_traffic()
+    prof_traffic = _profile_traffic() if args.storage == "f32" else None
     if prof_traffic:
         roof["traffic"] = prof_traffic
+        roof["traffic_over_algorithmic"] = round(prof_traffic / algo_bytes, 4)
 
     out = {"metric": "MLUPS", "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+           "timed_runs_ms": [round(r, 4) for r in runs], "timed_runs": REPEATS,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic",
            "config": {"workload": "D3Q19 BGK lid-driven cavity 256^3, FP32 storage, halfway bounce-back "
@@ -244,7 +263,7 @@ def _profile_traffic():
     p = os.path.join(ROOT, "profiles", "stream_collide_d3q19_cavity.txt")
     try:
         for line in open(p):
-            if line.startswith("traffic_bytes_per_launch_256cube:"):
+            if line.strip().startswith("traffic_bytes_per_launch_256cube:"):
                 return float(line.split(":")[1])
     except OSError:
         pass
@@ -305,6 +324,34 @@ def extras(args, torch, X, I, stream):
         sim.close()
     del mask
 
+    # Section 4.2's high-Reynolds cavity: D3Q27 KBC with a regularized moving
+    # lid (INLET cells on the top plane, inward normal -z, u = (0.06, 0, 0)),
+    # 128^3, Re = 10,000; a stability demonstration (no reference data):
+    # 20,000 steps must stay finite
+    try:
+        n3, U3, re3 = 128, 0.06, 10000.0
+        om3 = 1.0 / (3.0 * U3 * (n3 - 2) / re3 + 0.5)
+        m3 = I.lid_driven_cavity_mask(n3)
+        m3[n3 - 1, 1:n3 - 1, 1:n3 - 1] = I.INLET
+        sim = X.Simulation(27, (n3, n3, n3), om3, "kbc", "f32", stream=stream.cuda_stream)
+        sim.set_mask(m3)
+        sim.set_bc(X.XLB_CELL_INLET, 1.0, (U3, 0.0, 0.0))
+        sim.set_inlet_scheme("regularized")
+        sim.set_inlet_normal(2, -1)
+        sim.init()
+        sim.step(1)
+        ms = timed(sim, 20000 - 1)
+        r3, u3 = sim.macroscopic()
+        sim.close()
+        fl3 = np.isin(m3, (0, 3, 4))
+        res["kbc_cavity128_re10000_regularized_lid"] = {
+            "steps": 20000, "omega": om3, "finite": bool(np.isfinite(u3).all() and np.isfinite(r3).all()),
+            "max_u_over_lid": float(np.abs(u3[:, fl3]).max() / U3), "mean_rho": float(r3[fl3].mean()),
+            "mlups": round(n3 ** 3 / (ms * 1e3), 1)}
+        del m3, r3, u3
+    except Exception as e:  # secondary figures; keep the line
+        res["kbc_cavity128_re10000_error"] = repr(e)
+
     # the same flow on the 128 x 64 x 64 crop (radius 8), 1000 steps, in the
     # three storage forms, against the FP64 oracle's velocity stored at
     # 16,384 sampled fluid cells by tests/golden/make_kbc_sphere_crop.py
@@ -337,34 +384,28 @@ def extras(args, torch, X, I, stream):
     rho0 = (1.0 + I.density_perturbation((m, m, m), 1e-3, seed=1234)).astype(np.float32)
     sim = X.Simulation(19, (m, m, m), 1.25, "bgk", "f32", stream=stream.cuda_stream)
     rho0_d = torch.from_numpy(rho0).cuda()
-    rho = torch.empty((m, m, m), dtype=torch.float32, device="cuda")
-    u = torch.empty((3, m, m, m), dtype=torch.float32, device="cuda")
-    g = torch.empty((m, m, m), dtype=torch.float32, device="cuda")
     box = (slice(48, 80),) * 3
 
     def gradient(profile):
-        sim.init(rho0_d, None)
-        X.xlb_tape_begin(sim.ctx, 500, 50)
-        sim.step(500)
-        X.xlb_macroscopic(sim.ctx, rho, u)
-        rb = torch.zeros_like(rho)
-        ub = torch.zeros_like(u)
-        rb[box] = 0.5 * (u[(slice(None),) + box] ** 2).sum(0)
-        ub[(slice(None),) + box] = rho[box] * u[(slice(None),) + box]
-        X.xlb_adjoint_seed_macro(sim.ctx, rb, ub)
+        # the differentiable rollout: tape, 500 steps, FP64 kinetic-energy
+        # loss on the device; backward seeds the adjoint with the loss
+        # cotangent (formed on the GPU) and returns dL/drho0
         X.xlb_profile_enable(sim.ctx, profile)
-        X.xlb_adjoint_step(sim.ctx, 500)
-        X.xlb_adjoint_init_grad(sim.ctx, g, None)
-        X.xlb_tape_end(sim.ctx)
+        r0 = rho0_d.clone().requires_grad_(True)
+        loss = X.rollout(sim, r0, 500, 50, box)
+        (grad,) = torch.autograd.grad(loss, [r0])
+        return loss, grad
 
     gradient(False)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    gradient(False)
+    loss, g = gradient(False)
     torch.cuda.synchronize()
     grad_s = time.perf_counter() - t0
     gradient(True)
     adj_ms, adj_n = X.xlb_profile_read(sim.ctx, 1)
+    res["adjoint_loss_fp64"] = float(loss)
+    res["adjoint_grad_norm"] = float(np.sqrt(X.xlb_sum_squares(sim.ctx, g)))  # FP64 on the GPU
     sim.close()
     cells = m ** 3
     if adj_n:
@@ -374,7 +415,6 @@ def extras(args, torch, X, I, stream):
     res["adjoint_d3q19_128_gradient_e2e_s"] = round(grad_s, 4)
     # forward + recompute + adjoint: about 3 updates per step of the rollout
     res["adjoint_d3q19_128_gradient_rollout_mlups"] = round(500 * cells / (grad_s * 1e6), 1)
-    res["adjoint_grad_norm"] = float(torch.linalg.vector_norm(g.double()).item())
 
     # batched channels: 4096 D2Q9 domains (32..256 x 32..128, 1-5 discs, body
     # force), autotuned launch shape, 5000 steps in one persistent CUDA-graph

@@ -52,7 +52,11 @@ enum { XLB_COLL_NONE = 0, XLB_COLL_BGK = 1, XLB_COLL_KBC = 2 };
 
 /* Storage precision of populations (Section 3.7 "compute/storage"): the
  * compute type is always FP32.  F16/BF16 store shifted populations
- * f_i - w_i rounded to nearest even (the centring Section 4.1 cites). */
+ * f_i - w_i (the centring Section 4.1 cites).  F16 rounds to nearest even.
+ * BF16 rounds stochastically (up with probability equal to the discarded
+ * fraction), from random bits hashed from the cell index and the cell's FP32
+ * values, so that results are reproducible and identical in every kernel
+ * variant; ghost values of boundary links round to nearest even. */
 enum { XLB_STORE_F32 = 0, XLB_STORE_F16 = 1, XLB_STORE_BF16 = 2 };
 
 /* Cell types of the mask (Section 3.5).  For a fluid-like or FWALL cell x
@@ -148,6 +152,18 @@ int xlb_set_inlet_profile(xlb_ctx* ctx, const float* u);
 enum { XLB_INLET_ZOU_HE = 0, XLB_INLET_REGULARIZED = 1 };
 int xlb_set_inlet_scheme(xlb_ctx* ctx, int scheme);
 
+/* Inward normal n = sign e_axis (axis 0 = x, 1 = y, 2 = z; sign +1 or -1)
+ * of the boundary the INLET cells lie on; (0, +1), an inflow along +x, by
+ * default.  INLET cells are velocity boundaries: the unknown populations are
+ * those entering the fluid through the boundary (c_i . n = +1), rho comes
+ * from the known ones, [sum_{c.n=0} f_i + 2 sum_{c.n=-1} f_i] / (1 - u.n), and
+ * the rule of xlb_set_inlet_scheme rebuilds them.  With a velocity parallel
+ * to the wall (e.g. normal (2, -1) on the top plane and u = (U, 0, 0)) the
+ * regularized rule is the regularized moving wall Section 4.2 uses for its
+ * lid.  Acts from the next step on; XLB_ERR_ARG for an axis beyond the
+ * lattice's dimension or another sign, XLB_ERR_STATE while a tape is open. */
+int xlb_set_inlet_normal(xlb_ctx* ctx, int axis, int sign);
+
 /* Curved no-slip walls: Bouzidi's linear interpolated bounce-back (Bouzidi,
  * Firdaouss and Lallemand 2001, named in Section 4.3) on listed links.
  * Link k joins FLUID cell cell[k] (index x + nx*(y + ny*z)) to its WALL
@@ -227,29 +243,52 @@ int xlb_macroscopic(xlb_ctx* ctx, float* rho, float* u);
  * shift).  Host outputs; synchronises. */
 int xlb_reduce(xlb_ctx* ctx, double out_mass[1], double out_mom[3]);
 
+/* FP64 kinetic energy L = sum over the box of (1/2) rho |u|^2 of the current
+ * post-stream state's observables (those xlb_macroscopic returns: u is the
+ * reported velocity (j + F/2) / rho, EQ cells count with their prescribed
+ * state, solid cells with zero) -- the rollout loss of the differentiable
+ * workloads (Section 6 takes gradients of such losses).  The box is
+ * [box_lo[a], box_hi[a]) per axis (x, y, z; 0 <= lo < hi <= extent, z range
+ * [0, 1) on D2Q9).  rho and u are formed in FP32, the squares and the sum in
+ * FP64.  out: one double, device memory (written asynchronously on the ctx
+ * stream) or host memory (synchronises). */
+int xlb_kinetic_energy(xlb_ctx* ctx, const int64_t box_lo[3], const int64_t box_hi[3], double* out);
+
+/* FP64 sum of squares of n floats in device memory (the squared norm of a
+ * gradient), on the ctx stream; out as for xlb_kinetic_energy.  XLB_ERR_ARG
+ * for host memory. */
+int xlb_sum_squares(xlb_ctx* ctx, const float* x, int64_t n, double* out);
+
 /* Wait for all work queued on the ctx's stream; XLB_ERR_TIMEOUT if a bounded
  * wait inside a kernel expired since the last check (the results of those
  * steps are invalid). */
 int xlb_synchronize(xlb_ctx* ctx);
 
 /* FP64 totals of stored populations without any device allocation.  The
- * paper has no counterpart: this serves callers that must not call
- * cudaMalloc (code capturing or replaying a CUDA graph, real-time loops that
- * pre-allocate everything, hosts that own all device memory through their
- * own pools).  It reduces `populations` (device memory: Q planes of
- * plane_stride elements of the storage type, each holding f_i - w_i for the
- * N = nx*ny*nz cells, x fastest -- the layout xlb_populations exposes) over
- * the fluid-like cells of `mask` (device memory, uint8 XLB_CELL_* codes; NULL
- * = all cells): out[0] = sum rho, out[1..3] = sum j.  `out` is 4 doubles in
- * device memory (written on the stream) or host memory (the call then
- * synchronises the stream).  The partial sums live in one fixed array of
- * 128 KiB compiled into the library, which every GPU that loads it keeps
- * until the process exits: at most 67,108,864 cells (4096 partial sums of
- * 16384 cells); larger lattices give XLB_ERR_ARG.  The first call on a device
- * looks up the array's address with that device current; make that first call
- * before capturing any stream.  Calls share the array: calls that overlap on
- * the GPU race, so order them on one stream.  Each call rewrites every
- * partial it reads, so nothing needs clearing between calls. */
+ * paper has no counterpart.  It serves callers that cannot call cudaMalloc:
+ * latency-critical loops (the allocator may synchronise the device and takes
+ * unbounded time), host frameworks that own all device memory through their
+ * own pools under a fixed budget, and recovery paths that run after the
+ * device has run out of memory.  It reduces `populations` (device memory: Q
+ * planes of plane_stride elements of the storage type, each holding
+ * f_i - w_i for the N = nx*ny*nz cells, x fastest -- the layout
+ * xlb_populations exposes) over the fluid-like cells of `mask` (device
+ * memory, uint8 XLB_CELL_* codes; NULL = all cells): out[0] = sum rho,
+ * out[1..3] = sum j, of the populations as stored.  After xlb_step the live
+ * buffer holds the post-collision state (the next update streams it), not
+ * the post-stream state xlb_reduce sums: the two totals agree on periodic
+ * lattices without a body force and differ with walls, inlets or a moving
+ * lid.  `out` is 4 doubles in device memory (written on the stream) or host
+ * memory (the call then copies and synchronises the stream, and returns
+ * XLB_ERR_ARG if the stream is being captured).  The partial sums live in
+ * one fixed array of 128 KiB compiled into the library, which every GPU that
+ * loads it keeps until the process exits: at most 67,108,864 cells (4096
+ * partial sums of 16384 cells); larger lattices give XLB_ERR_ARG.  The first
+ * call on a device looks up the array's address with that device current;
+ * make that first call before capturing any stream.  Calls share the array:
+ * calls that overlap on the GPU race, so order them on one stream.  Each call
+ * rewrites every partial it reads, so nothing needs clearing between
+ * calls. */
 int xlb_moments_noalloc(int lattice, const int64_t dims[3], int storage, const void* populations,
                         int64_t plane_stride, const uint8_t* mask, double* out, void* cuda_stream);
 
@@ -275,14 +314,22 @@ int xlb_populations(xlb_ctx* ctx, void** dev_ptr, int64_t* plane_stride);
 
 /* Open a tape right after xlb_init: the next xlb_step calls (n_steps in
  * total) record a checkpoint every checkpoint_every steps.  The adjoint then
- * recomputes each segment from its checkpoint.  BGK or NONE collision; masks
- * with INLET / OUTLET / FWALL cells are XLB_ERR_UNSUPPORTED. */
+ * recomputes each segment from its checkpoint.  BGK or NONE collision, FP32
+ * or FP16 storage (the FP16 gradient is that of the FP16 forward, each
+ * rounding taken as the identity); BF16 storage and masks with INLET /
+ * OUTLET / FWALL cells are XLB_ERR_UNSUPPORTED. */
 int xlb_tape_begin(xlb_ctx* ctx, int64_t n_steps, int64_t checkpoint_every);
 
 /* Seed the adjoint at the final step with the loss cotangents of the
  * observables xlb_macroscopic returns: dL_drho (N) and dL_du (D*N); either
  * may be NULL (zero).  Requires all n_steps of the tape to have been taken. */
 int xlb_adjoint_seed_macro(xlb_ctx* ctx, const float* dL_drho, const float* dL_du);
+
+/* Seed the adjoint at the final step with scale times the cotangent of the
+ * kinetic-energy loss of xlb_kinetic_energy over the same box, formed on the
+ * GPU from the final state: dL/drho = |u|^2 / 2 and dL/du = rho u inside the
+ * box, zero outside.  Same preconditions as xlb_adjoint_seed_macro. */
+int xlb_adjoint_seed_kinetic_energy(xlb_ctx* ctx, const int64_t box_lo[3], const int64_t box_hi[3], double scale);
 
 /* Propagate the adjoint n steps backwards (n <= steps remaining). */
 int xlb_adjoint_step(xlb_ctx* ctx, int64_t n);
@@ -307,12 +354,14 @@ int xlb_tape_release(xlb_ctx* ctx);
  *     global memory;
  *   XLB_KERNEL_VEC:    4 consecutive cells per thread, one aligned 4-wide load
  *     per direction, the +-x neighbour element exchanged by warp shuffles
- *     (16-bit storage, D2Q9 / D3Q19, BGK / NONE, nx % 4 == 0);
+ *     (16-bit storage, D2Q9 / D3Q19, BGK, nx % 4 == 0);
+ *   XLB_KERNEL_VEC2:   the same with 2 cells per thread and 32-bit words
+ *     (nx even; chosen only on request);
  *   XLB_KERNEL_AUTO:   VEC where possible on lattices without boundary faces
  *     (whole face planes the mask fills with one boundary type), else DIRECT
  *     (the default).
  * A mask with an FWALL face plane always runs DIRECT. */
-enum { XLB_KERNEL_AUTO = 0, XLB_KERNEL_DIRECT = 1, XLB_KERNEL_VEC = 2 };
+enum { XLB_KERNEL_AUTO = 0, XLB_KERNEL_DIRECT = 1, XLB_KERNEL_VEC = 2, XLB_KERNEL_VEC2 = 3 };
 
 /* Choose the variant (XLB_ERR_UNSUPPORTED if it cannot run this ctx). */
 int xlb_set_kernel(xlb_ctx* ctx, int variant);

@@ -40,8 +40,9 @@ Readings of points the paper leaves open:
 * halfway bounce-back for WALL (stationary) and LID (moving, with the
   momentum term 2 w_i rho_w (c_i . u_w) / c_s^2 and rho_w fixed);
 * EQ cells hold f^eq(rho_w, u_w) (the equilibrium BC of Section 3.5 / 5);
-* INLET cells apply Zou-He velocity reconstruction for the populations with
-  c_x = +1 (non-equilibrium bounce-back of every unknown, no transverse term);
+* INLET cells are velocity boundaries (inward normal +x unless set): Zou-He
+  reconstruction of the populations entering the fluid (non-equilibrium
+  bounce-back of every unknown, no transverse term), or the regularized rule;
 * OUTLET cells copy their c_x = -1 populations from the cell at x-1
   (zero-gradient extrapolation);
 * observables are those of the post-stream state f_t; the reported velocity
@@ -270,10 +271,15 @@ class BC:
                       (those links keep halfway bounce-back, q = 1/2).
     inlet_scheme:     "zou_he" or "regularized", the two inflow rules Section
                       4.3 names for INLET cells.
+    inlet_normal:     (axis, sign): the direction n = sign e_axis from the
+                      INLET cells' boundary into the fluid; (0, +1), inflow
+                      along +x, by default.  INLET cells are velocity
+                      boundaries: with the velocity parallel to the wall they
+                      are a moving wall (the regularized lid of Section 4.2).
     """
 
     def __init__(self, d, lid_u=None, lid_rho=1.0, inlet_u=None, eq_rho=1.0, eq_u=None, wall_q=None,
-                 inlet_scheme="zou_he"):
+                 inlet_scheme="zou_he", inlet_normal=(0, 1)):
         z = [0.0] * d
         self.lid_u = list(lid_u) if lid_u is not None else z
         self.lid_rho = lid_rho
@@ -287,6 +293,7 @@ class BC:
         self.eq_u = list(eq_u) if eq_u is not None else z
         self.wall_q = wall_q
         self.inlet_scheme = inlet_scheme  # "zou_he" | "regularized"
+        self.inlet_normal = (int(inlet_normal[0]), int(inlet_normal[1]))
 
 
 def _const_feq(lat, rho, u):
@@ -340,47 +347,57 @@ def pull_plain(lat: Lattice, h, mask, bc: BC):
     return np.stack(out)
 
 
+def _inlet_setup(lat: Lattice, mask, bc: BC):
+    """Velocity boundary at INLET cells with inward normal n = sign e_axis:
+    c.n of every direction, the prescribed velocity field and the density
+    from the known populations (those with c.n <= 0),
+      rho = [sum_{c.n=0} f_i + 2 sum_{c.n=-1} f_i] / (1 - u.n)."""
+    axis, sign = bc.inlet_normal
+    cn = sign * lat.c[:, axis]
+    uin = np.stack([np.broadcast_to(np.asarray(bc.inlet_u[a], dtype=float), mask.shape)
+                    for a in range(lat.d)])
+    return cn, uin, sign * uin[axis]
+
+
 def zou_he_inlet(lat: Lattice, f, mask, bc: BC):
-    """Zou-He velocity inlet on INLET cells, inflow along +x (unknown
-    populations are those with c_x = +1):
-      rho = [sum_{c_x=0} f_i + 2 sum_{c_x=-1} f_i] / (1 - u_x),
+    """Zou-He velocity boundary on INLET cells: the unknown populations are
+    those entering the fluid through the boundary (c_i . n = +1; with the
+    default normal, the inflow along +x, c_x = +1):
+      rho = [sum_{c.n=0} f_i + 2 sum_{c.n=-1} f_i] / (1 - u.n),
       f_i = f_opp(i) + f_i^eq(rho, u) - f_opp(i)^eq(rho, u) for each unknown i."""
-    cx = lat.c[:, 0]
     sel = mask == INLET
     if not sel.any():
         return f
     f = f.copy()
-    uin = np.stack([np.broadcast_to(np.asarray(bc.inlet_u[a], dtype=float), mask.shape)
-                    for a in range(lat.d)])
-    rho = (sum(f[i] for i in range(lat.q) if cx[i] == 0)
-           + 2.0 * sum(f[i] for i in range(lat.q) if cx[i] == -1)) / (1.0 - uin[0])
+    cn, uin, un = _inlet_setup(lat, mask, bc)
+    rho = (sum(f[i] for i in range(lat.q) if cn[i] == 0)
+           + 2.0 * sum(f[i] for i in range(lat.q) if cn[i] == -1)) / (1.0 - un)
     feq = equilibrium(lat, rho, uin)
     for i in range(lat.q):
-        if cx[i] == 1:
+        if cn[i] == 1:
             j = lat.opp[i]
             f[i] = np.where(sel, f[j] + feq[i] - feq[j], f[i])
     return f
 
 
 def regularized_inlet(lat: Lattice, f, mask, bc: BC):
-    """Regularized velocity inlet of Latt et al. (2008), the second inflow
-    rule Section 4.3 names, on INLET cells (inflow along +x, unknowns c_x = +1):
+    """Regularized velocity boundary of Latt et al. (2008), the second inflow
+    rule Section 4.3 names (and, as a moving wall, the regularized lid of
+    Section 4.2), on INLET cells (unknowns c_i . n = +1):
       rho as in the Zou-He rule; f^neq_i = f_i - f_i^eq(rho, u) for the known
       populations and f^neq_i = f^neq_opp(i) for the unknown ones;
       Pi = sum_i c_i c_i f^neq_i; then every population is replaced by
       f_i = f_i^eq(rho, u) + w_i / (2 cs^4) (c_i c_i - cs^2 I) : Pi."""
-    cx = lat.c[:, 0]
     sel = mask == INLET
     if not sel.any():
         return f
-    uin = np.stack([np.broadcast_to(np.asarray(bc.inlet_u[a], dtype=float), mask.shape)
-                    for a in range(lat.d)])
-    rho = (sum(f[i] for i in range(lat.q) if cx[i] == 0)
-           + 2.0 * sum(f[i] for i in range(lat.q) if cx[i] == -1)) / (1.0 - uin[0])
+    cn, uin, un = _inlet_setup(lat, mask, bc)
+    rho = (sum(f[i] for i in range(lat.q) if cn[i] == 0)
+           + 2.0 * sum(f[i] for i in range(lat.q) if cn[i] == -1)) / (1.0 - un)
     feq = equilibrium(lat, rho, uin)
     neq = f - feq
     for i in range(lat.q):
-        if cx[i] == 1:
+        if cn[i] == 1:
             neq[i] = neq[lat.opp[i]]
     Pi = [[sum(lat.c[i, a] * lat.c[i, b] * neq[i] for i in range(lat.q)) for b in range(lat.d)]
           for a in range(lat.d)]

@@ -22,6 +22,12 @@ struct AdjointArgs {
   float* grad_rho;
   float* grad_u;
   long long ucs;            // component stride of vector fields
+  // ADJ_SEED with ke = 1: the cotangents are those of the kinetic energy
+  // (1/2) rho |u|^2 summed over the box [box_lo, box_hi) (times scale), formed
+  // in the kernel: dL/drho = |u|^2 / 2, dL/du = rho u inside the box
+  int ke;
+  int box_lo[3], box_hi[3];
+  float scale;
   void* stream;
 };
 

@@ -139,11 +139,11 @@ __device__ __forceinline__ void init_state(const float* rho0, const float* u0, l
   const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const float drho = rho - 1.0f;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    S s;
-    Store<S>::st(&s, weight<Q>(i) * (drho + rho * eq_poly<Q>(i, u, usq)));
-    df[i] = Store<S>::ld_plain(&s);
-  }
+  for (int i = 0; i < Q; ++i) df[i] = weight<Q>(i) * (drho + rho * eq_poly<Q>(i, u, usq));
+  CellRound<S> rnd;
+  rnd.begin((uint32_t)self, df);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) df[i] = rnd.rounded(i, df[i]);
 }
 
 template <int Q, typename S, int COLL>
@@ -190,11 +190,15 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_adjoint_step0(const float* __rest
 }
 
 // dL/df_T = rbar + ubar . (c_i - u) / rho for the observables of the readout
-// (u is the reported velocity (j + F/2) / rho under a body force).
-template <int Q, typename S>
+// (u is the reported velocity (j + F/2) / rho under a body force).  The
+// cotangents rbar, ubar are read from the given fields, or, with KE, are
+// those of the kinetic energy over the box [lo, hi): scale * |u|^2 / 2 and
+// scale * rho u inside it, zero outside.
+template <int Q, typename S, bool KE>
 __global__ void __launch_bounds__(ROW_BLOCK) k_adjoint_seed(const S* __restrict__ h, const float* __restrict__ rbar,
                                                             const float* __restrict__ ubar, long long ucs,
-                                                            float* __restrict__ aout, const StepParams p) {
+                                                            float* __restrict__ aout, const StepParams p, int3 lo,
+                                                            int3 hi, float scale) {
   CellIdx c;
   if (!cell_of_block(p, c)) return;
   const int fl = p.has_mask ? p.flags[c.self] : 0;
@@ -213,12 +217,21 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_adjoint_seed(const S* __restrict_
   }
   const float rho = 1.0f + drho, ir = 1.0f / rho;
   const float u[3] = {j[0] * ir, j[1] * ir, Lattice<Q>::D == 3 ? j[2] * ir : 0.f};
-  const float rb = rbar ? rbar[c.self] : 0.f;
-  float ub[3] = {0.f, 0.f, 0.f};
-  if (ubar) {
-    ub[0] = ubar[c.self];
-    ub[1] = ubar[ucs + c.self];
-    if (Lattice<Q>::D == 3) ub[2] = ubar[2 * ucs + c.self];
+  float rb = 0.f, ub[3] = {0.f, 0.f, 0.f};
+  if (KE) {
+    if (c.x >= lo.x && c.x < hi.x && c.y >= lo.y && c.y < hi.y && c.z >= lo.z && c.z < hi.z) {
+      rb = scale * 0.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      ub[0] = scale * rho * u[0];
+      ub[1] = scale * rho * u[1];
+      ub[2] = scale * rho * u[2];
+    }
+  } else {
+    rb = rbar ? rbar[c.self] : 0.f;
+    if (ubar) {
+      ub[0] = ubar[c.self];
+      ub[1] = ubar[ucs + c.self];
+      if (Lattice<Q>::D == 3) ub[2] = ubar[2 * ucs + c.self];
+    }
   }
   const float ubu = ub[0] * u[0] + ub[1] * u[1] + ub[2] * u[2];
 #pragma unroll
@@ -273,10 +286,17 @@ int launch_adj_typed(AdjOp op, const AdjointArgs& a) {
   const dim3 grid((unsigned)nblk), block(ROW_BLOCK);
   cudaStream_t st = (cudaStream_t)a.stream;
   switch (op) {
-    case ADJ_SEED:
-      k_adjoint_seed<Q, S><<<grid, block, 0, st>>>((const S*)a.state, a.fields_in, a.fields_in2, a.ucs, a.abar_out,
-                                                   p);
+    case ADJ_SEED: {
+      const int3 lo = make_int3(a.box_lo[0], a.box_lo[1], a.box_lo[2]);
+      const int3 hi = make_int3(a.box_hi[0], a.box_hi[1], a.box_hi[2]);
+      if (a.ke)
+        k_adjoint_seed<Q, S, true><<<grid, block, 0, st>>>((const S*)a.state, nullptr, nullptr, a.ucs, a.abar_out,
+                                                           p, lo, hi, a.scale);
+      else
+        k_adjoint_seed<Q, S, false><<<grid, block, 0, st>>>((const S*)a.state, a.fields_in, a.fields_in2, a.ucs,
+                                                            a.abar_out, p, lo, hi, 1.0f);
       return 0;
+    }
     case ADJ_STEP:
       if (a.coll == COLL_NONE)
         k_adjoint_step<Q, S, COLL_NONE><<<grid, block, 0, st>>>((const S*)a.state, a.abar_in, a.abar_out, p);

@@ -51,6 +51,7 @@ struct xlb_ctx {
   float* link_q = nullptr;  // Bouzidi wall distance per link (LINK_BZ entries), or null
   float* inlet_field = nullptr;  // D * N inlet velocities (xlb_set_inlet_profile), or null
   int inlet_scheme = XLB_INLET_ZOU_HE;
+  int inlet_axis = 0, inlet_sign = 1;  // inward normal of the INLET boundary
   bool has_inlet_outlet = false;  // INLET, OUTLET or FWALL cells (no adjoint)
   float* init_fields = nullptr;  // (1 + D) * N: rho0, u0 (component-major)
   bool has_init = false;
@@ -169,6 +170,8 @@ static StepParams make_params(const xlb_ctx* c) {
   p.eq_rho = c->eq_rho;
   p.inlet_field = c->inlet_field;
   p.inlet_regularized = c->inlet_scheme == XLB_INLET_REGULARIZED;
+  p.inlet_axis = c->inlet_axis;
+  p.inlet_sign = c->inlet_sign;
   p.err = c->err_word ? c->err_word + 1 : nullptr;
   p.has_faces = 0;
   for (int f = 0; f < 6; ++f) {
@@ -243,8 +246,8 @@ static void prof_end(xlb_ctx* c, cudaEvent_t* b) {
 // The vectorised bulk kernel (4 cells per thread) runs 16-bit storage with
 // BGK or NONE collision on D2Q9 / D3Q19 when nx is a multiple of 4; FP32 is
 // fastest with one cell per thread (measured on the 256^3 cavity).
-static bool vec_possible(const xlb_ctx* c) {
-  return c->esize == 2 && c->Q != 27 && c->coll != XLB_COLL_KBC && c->nx % 4 == 0;
+static bool vec_possible(const xlb_ctx* c, int width = 4) {
+  return c->esize == 2 && c->Q != 27 && c->coll == XLB_COLL_BGK && c->nx % width == 0;
 }
 
 // The vectorised kernel has no full-way reversal for FWALL face planes.
@@ -258,6 +261,7 @@ static bool has_fwall_face(const xlb_ctx* c) {
 // warp of a 4-cell-per-thread row holds a face-adjacent lane (measured slower
 // than one cell per thread on the 256^3 cavity).
 static bool use_vec(const xlb_ctx* c) {
+  if (c->variant == XLB_KERNEL_VEC2) return vec_possible(c, 2) && !has_fwall_face(c);
   if (c->variant == XLB_KERNEL_DIRECT || !vec_possible(c) || has_fwall_face(c)) return false;
   if (c->variant == XLB_KERNEL_VEC) return true;
   for (int f = 0; f < 6; ++f)
@@ -268,8 +272,22 @@ static bool use_vec(const xlb_ctx* c) {
 // Boundary pass on dst after a pass that produced post-collision values
 // there: ghost values of every link and of the inlet / outlet cells' links;
 // with `fix_src`, the inlet / outlet cells are first recomputed from it.
+// Without it (the state came from a local collision or a restore, not from
+// the bulk kernel, which pushes them itself), the ghost values of the
+// boundary faces are written first.
 static int boundary_pass(xlb_ctx* c, const void* fix_src, void* dst) {
-  if (!c->has_mask || c->n_links + c->n_fix == 0) return XLB_OK;
+  if (!c->has_mask) return XLB_OK;
+  if (!fix_src) {
+    bool faces = false;
+    for (int f = 0; f < 6; ++f) faces |= c->face[f] != 0;
+    if (faces) {
+      LaunchArgs g = base_args(c);
+      g.dst = dst;
+      const int r = dispatch(c, OP_FACE_GHOSTS, g);
+      if (r) return r;
+    }
+  }
+  if (c->n_links + c->n_fix == 0) return XLB_OK;
   LaunchArgs a = base_args(c);
   a.src = fix_src ? fix_src : dst;
   a.dst = dst;
@@ -292,6 +310,7 @@ static int launch_step(xlb_ctx* c, const void* src, void* dst) {
   LaunchArgs a = base_args(c);
   a.src = src;
   a.dst = dst;
+  a.vec_width = c->variant == XLB_KERNEL_VEC2 ? 2 : 4;
   a.p.has_mask = 0;  // bulk pass: every cell pulled as if periodic
   cudaEvent_t* pe = prof_begin(c, 0);
   int r = dispatch(c, vec ? OP_STEP_VEC : OP_STEP, a);
@@ -719,6 +738,19 @@ int xlb_set_inlet_scheme(xlb_ctx* c, int scheme) {
   return XLB_OK;
 }
 
+int xlb_set_inlet_normal(xlb_ctx* c, int axis, int sign) {
+  if (!c) return XLB_ERR_ARG;
+  if (axis < 0 || axis >= c->D || (sign != 1 && sign != -1))
+    return fail(c, XLB_ERR_ARG, "normal: axis in [0, %d), sign +1 or -1", c->D);
+  if (c->tape_open) return fail(c, XLB_ERR_STATE, "boundary values cannot change while a tape is open");
+  const int r = materialize_post_stream(c);  // f_t with the old normal
+  if (r) return r;
+  c->inlet_axis = axis;
+  c->inlet_sign = sign;
+  ++c->epoch;
+  return XLB_OK;
+}
+
 int xlb_set_wall_distances(xlb_ctx* c, int64_t n, const int64_t* cell, const int32_t* dir, const float* q) {
   if (!c) return XLB_ERR_ARG;
   if (n < 0 || (n > 0 && (!cell || !dir || !q))) return fail(c, XLB_ERR_ARG, "n < 0 or a null array");
@@ -974,11 +1006,14 @@ int xlb_synchronize(xlb_ctx* c) {
 
 int xlb_set_kernel(xlb_ctx* c, int variant) {
   if (!c) return XLB_ERR_ARG;
-  if (variant < XLB_KERNEL_AUTO || variant > XLB_KERNEL_VEC)
+  if (variant < XLB_KERNEL_AUTO || variant > XLB_KERNEL_VEC2)
     return fail(c, XLB_ERR_ARG, "unknown kernel variant %d", variant);
   if (variant == XLB_KERNEL_VEC && !vec_possible(c))
     return fail(c, XLB_ERR_UNSUPPORTED,
-                "the vectorised kernel needs 16-bit storage, D2Q9 or D3Q19, BGK/NONE and nx %% 4 == 0");
+                "the vectorised kernel needs 16-bit storage, D2Q9 or D3Q19, BGK and nx %% 4 == 0");
+  if (variant == XLB_KERNEL_VEC2 && !vec_possible(c, 2))
+    return fail(c, XLB_ERR_UNSUPPORTED,
+                "the 2-wide vectorised kernel needs 16-bit storage, D2Q9 or D3Q19, BGK and even nx");
   c->variant = variant;
   ++c->epoch;
   return XLB_OK;
@@ -986,7 +1021,7 @@ int xlb_set_kernel(xlb_ctx* c, int variant) {
 
 int xlb_get_kernel(const xlb_ctx* c, int* variant) {
   if (!c || !variant) return XLB_ERR_ARG;
-  *variant = use_vec(c) ? XLB_KERNEL_VEC : XLB_KERNEL_DIRECT;
+  *variant = use_vec(c) ? (c->variant == XLB_KERNEL_VEC2 ? XLB_KERNEL_VEC2 : XLB_KERNEL_VEC) : XLB_KERNEL_DIRECT;
   return XLB_OK;
 }
 
@@ -1026,9 +1061,13 @@ int xlb_reduce(xlb_ctx* c, double out_mass[1], double out_mom[3]) {
   LaunchArgs a = base_args(c);
   a.src = c->buf[c->cur];
   a.kind_h = c->kind_h;
+  long long b = (c->N + 127) / 128;
+  if (b > c->partial_cap) b = c->partial_cap;
+  if (b < 1) b = 1;
+  a.partial_capacity = b;
   int r = dispatch(c, OP_REDUCE_PARTIAL, a);
   if (r) return r;
-  launch_reduce_final(c->partial, row_blocks(a.p), c->red_out, c->stream);
+  launch_reduce_final(c->partial, b, c->red_out, c->stream);
   double h[4];
   CK(cudaMemcpyAsync(h, c->red_out, sizeof h, cudaMemcpyDeviceToHost, c->stream));
   r = check_device_error(c);
@@ -1037,6 +1076,66 @@ int xlb_reduce(xlb_ctx* c, double out_mass[1], double out_mom[3]) {
   if (out_mom)
     for (int k = 0; k < 3; ++k) out_mom[k] = h[1 + k];
   return XLB_OK;
+}
+
+// Box [lo, hi) of a kinetic-energy loss: per axis 0 <= lo < hi <= extent
+// (z: 0 and 1 on D2Q9).
+static int check_box(xlb_ctx* c, const int64_t lo[3], const int64_t hi[3]) {
+  if (!lo || !hi) return fail(c, XLB_ERR_ARG, "box bounds are null");
+  const int64_t ext[3] = {c->nx, c->ny, c->nz};
+  for (int a = 0; a < 3; ++a)
+    if (lo[a] < 0 || hi[a] <= lo[a] || hi[a] > ext[a])
+      return fail(c, XLB_ERR_ARG, "box axis %d: need 0 <= lo < hi <= %lld", a, (long long)ext[a]);
+  return XLB_OK;
+}
+
+// Copy the FP64 result in red_out[0] to out: a device pointer asynchronously
+// on the ctx stream, a host pointer synchronously.
+static int deliver_scalar(xlb_ctx* c, double* out) {
+  if (is_device_ptr(out)) {
+    CK(cudaMemcpyAsync(out, c->red_out, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    return XLB_OK;
+  }
+  double h[4];
+  CK(cudaMemcpyAsync(h, c->red_out, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  int r = check_device_error(c);
+  if (r) return r;
+  out[0] = h[0];
+  return XLB_OK;
+}
+
+int xlb_kinetic_energy(xlb_ctx* c, const int64_t box_lo[3], const int64_t box_hi[3], double* out) {
+  if (!c) return XLB_ERR_ARG;
+  if (!out) return fail(c, XLB_ERR_ARG, "out is null");
+  int r = check_box(c, box_lo, box_hi);
+  if (r) return r;
+  LaunchArgs a = base_args(c);
+  a.src = c->buf[c->cur];
+  a.kind_h = c->kind_h;
+  for (int k = 0; k < 3; ++k) {
+    a.box_lo[k] = (int)box_lo[k];
+    a.box_ext[k] = (int)(box_hi[k] - box_lo[k]);
+  }
+  const long long nbox = (long long)a.box_ext[0] * a.box_ext[1] * a.box_ext[2];
+  long long b = (nbox + 127) / 128;
+  if (b > c->partial_cap) b = c->partial_cap;
+  if (b < 1) b = 1;
+  a.partial_capacity = b;
+  r = dispatch(c, OP_KE_PARTIAL, a);
+  if (r) return r;
+  launch_reduce_final(c->partial, b, c->red_out, c->stream);
+  return deliver_scalar(c, out);
+}
+
+int xlb_sum_squares(xlb_ctx* c, const float* x, int64_t n, double* out) {
+  if (!c) return XLB_ERR_ARG;
+  if (!x || !out || n < 0) return fail(c, XLB_ERR_ARG, "x or out is null, or n < 0");
+  if (n > 0 && !is_device_ptr(x)) return fail(c, XLB_ERR_ARG, "x must be device memory");
+  const long long b = launch_sum_squares(x, n, c->partial, c->partial_cap > 0 ? c->partial_cap : 1, c->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "sum of squares launch");
+  launch_reduce_final(c->partial, b, c->red_out, c->stream);
+  return deliver_scalar(c, out);
 }
 
 // Serialized state: 64-byte header then the raw population buffer.
@@ -1135,6 +1234,9 @@ int xlb_tape_begin(xlb_ctx* c, int64_t n_steps, int64_t k) {
   if (n_steps < 1 || k < 1) return fail(c, XLB_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
   if (c->t != 0 || c->kind_h || !c->has_init) return fail(c, XLB_ERR_STATE, "open a tape right after xlb_init");
   if (c->coll == XLB_COLL_KBC) return fail(c, XLB_ERR_UNSUPPORTED, "the adjoint covers BGK and NONE collisions");
+  if (c->storage == XLB_STORE_BF16)
+    return fail(c, XLB_ERR_UNSUPPORTED,
+                "the adjoint covers FP32 and FP16 storage (with BF16 the gradient misses the 5e-3 storage bound)");
   if (c->has_inlet_outlet)
     return fail(c, XLB_ERR_UNSUPPORTED, "the adjoint does not cover inlet/outlet or full-way (FWALL) cells");
   xlb_tape_end(c);
@@ -1217,6 +1319,28 @@ int xlb_adjoint_seed_macro(xlb_ctx* c, const float* drho, const float* du) {
   a.fields_in = dr;
   a.fields_in2 = duu;
   a.abar_out = c->abar[0];
+  r = adispatch(c, ADJ_SEED, a);
+  if (r) return r;
+  c->acur = 0;
+  c->adj_t = c->tape_T;
+  return XLB_OK;
+}
+
+int xlb_adjoint_seed_kinetic_energy(xlb_ctx* c, const int64_t box_lo[3], const int64_t box_hi[3], double scale) {
+  if (!c) return XLB_ERR_ARG;
+  if (!c->tape_open) return fail(c, XLB_ERR_STATE, "no tape open");
+  if (c->t != c->tape_T || !c->kind_h) return fail(c, XLB_ERR_STATE, "take all %lld taped steps first", (long long)c->tape_T);
+  int r = check_box(c, box_lo, box_hi);
+  if (r) return r;
+  AdjointArgs a = adjoint_args(c);
+  a.state = c->buf[c->cur];
+  a.abar_out = c->abar[0];
+  a.ke = 1;
+  a.scale = (float)scale;
+  for (int k = 0; k < 3; ++k) {
+    a.box_lo[k] = (int)box_lo[k];
+    a.box_hi[k] = (int)box_hi[k];
+  }
   r = adispatch(c, ADJ_SEED, a);
   if (r) return r;
   c->acur = 0;

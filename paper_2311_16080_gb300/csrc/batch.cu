@@ -66,8 +66,10 @@ __device__ __forceinline__ void batch_domain_step(const S* __restrict__ src, S* 
     }
     collide<9, COLL_BGK>(df, p);
     if ((f & FLAG_TYPE) == FLUID) {
+      CellRound<S> rnd;
+      rnd.begin((uint32_t)(d.off + cell), df);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) Store<S>::st_l2(dst + (long long)i * d.plane + cell, df[i]);
+      for (int i = 0; i < 9; ++i) rnd.st_l2(dst + (long long)i * d.plane + cell, i, df[i]);
     }
   }
 }
@@ -136,9 +138,12 @@ __global__ void k_batch_single(const BatchDom* __restrict__ doms, int dom, const
     }
   }
   collide<9, COLL_BGK>(df, p);
-  if ((f & FLAG_TYPE) == FLUID)
+  if ((f & FLAG_TYPE) == FLUID) {
+    CellRound<S> rnd;
+    rnd.begin((uint32_t)(d.off + cell), df);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store<S>::st_l2(dst + (long long)i * d.plane + cell, df[i]);
+    for (int i = 0; i < 9; ++i) rnd.st_l2(dst + (long long)i * d.plane + cell, i, df[i]);
+  }
 }
 
 // f_0 = f^eq(rho, u) per cell (all domains in one launch over the
@@ -159,10 +164,13 @@ __global__ void k_batch_init(const BatchDom* __restrict__ doms, const int* __res
   float v[3] = {u ? u[2 * g] : 0.f, u ? u[2 * g + 1] : 0.f, 0.f};
   const bool fluid = (flags[d.foff + cell] & FLAG_TYPE) == FLUID;
   const float usq = v[0] * v[0] + v[1] * v[1];
+  float df[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i)
-    Store<S>::st(A + d.off + (long long)i * d.plane + cell,
-                 fluid ? weight<9>(i) * ((r - 1.0f) + r * eq_poly<9>(i, v, usq)) : 0.f);
+  for (int i = 0; i < 9; ++i) df[i] = fluid ? weight<9>(i) * ((r - 1.0f) + r * eq_poly<9>(i, v, usq)) : 0.f;
+  CellRound<S> rnd;
+  rnd.begin((uint32_t)(d.off + cell), df);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) rnd.st(A + d.off + (long long)i * d.plane + cell, i, df[i]);
 }
 
 // rho and reported u = (j + F/2) / rho per cell (0 on WALL cells), from the
@@ -234,8 +242,10 @@ __global__ void k_batch_collide(const BatchDom* __restrict__ doms, const int* __
 #pragma unroll
   for (int i = 0; i < 9; ++i) df[i] = Store<S>::ld_plain(a + (long long)i * d.plane);
   collide<9, COLL_BGK>(df, p);
+  CellRound<S> rnd;
+  rnd.begin((uint32_t)(d.off + cell), df);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) Store<S>::st(a + (long long)i * d.plane, df[i]);
+  for (int i = 0; i < 9; ++i) rnd.st(a + (long long)i * d.plane, i, df[i]);
 }
 
 // Flags: type | FLAG_SLOW for FLUID cells with a WALL cell in the stencil;

@@ -28,8 +28,7 @@ static bool kbc_op(Op op, const LaunchArgs& a) {
 
 #define XLB_ADJ(Q) \
   int launch_adj_q##Q##_s0(AdjOp, const AdjointArgs&); \
-  int launch_adj_q##Q##_s1(AdjOp, const AdjointArgs&); \
-  int launch_adj_q##Q##_s2(AdjOp, const AdjointArgs&);
+  int launch_adj_q##Q##_s1(AdjOp, const AdjointArgs&);
 XLB_ADJ(9)
 XLB_ADJ(19)
 #undef XLB_ADJ
@@ -57,13 +56,13 @@ int launch_d2q9(Op op, const LaunchArgs& a) { return fwd(9, op, a); }
 int launch_d3q19(Op op, const LaunchArgs& a) { return fwd(19, op, a); }
 int launch_d3q27(Op op, const LaunchArgs& a) { return fwd(27, op, a); }
 
-// The adjoint is provided for D2Q9 and D3Q19 (the differentiable workloads).
+// The adjoint is provided for D2Q9 and D3Q19 (the differentiable workloads)
+// with FP32 and FP16 storage.
 int launch_adjoint(AdjOp op, const AdjointArgs& a) {
   const int s = a.storage;
-  if (s < 0 || s > 2) return -5;
-  if (a.Q == 9) return s == 0 ? launch_adj_q9_s0(op, a) : s == 1 ? launch_adj_q9_s1(op, a) : launch_adj_q9_s2(op, a);
-  if (a.Q == 19)
-    return s == 0 ? launch_adj_q19_s0(op, a) : s == 1 ? launch_adj_q19_s1(op, a) : launch_adj_q19_s2(op, a);
+  if (s < 0 || s > 1) return -5;
+  if (a.Q == 9) return s == 0 ? launch_adj_q9_s0(op, a) : launch_adj_q9_s1(op, a);
+  if (a.Q == 19) return s == 0 ? launch_adj_q19_s0(op, a) : launch_adj_q19_s1(op, a);
   return -6;
 }
 

@@ -8,6 +8,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "launch.h"
 #include "lbm_device.cuh"
 
@@ -32,6 +34,18 @@ __device__ __forceinline__ bool cell_of_block(const StepParams& p, CellIdx& c) {
   return true;
 }
 
+// Cell of a bulk-kernel thread: on a (x-blocks, ny, nz) grid when p.grid3,
+// else on the grid flattened over rows (cell_of_block).
+__device__ __forceinline__ bool cell_of_grid(const StepParams& p, CellIdx& c) {
+  if (!p.grid3) return cell_of_block(p, c);
+  c.x = (int)(blockIdx.x * ROW_BLOCK + threadIdx.x);
+  if (c.x >= p.nx) return false;
+  c.y = (int)blockIdx.y;
+  c.z = (int)blockIdx.z;
+  c.self = c.x + p.nx * (c.y + p.ny * c.z);
+  return true;
+}
+
 // Blocks per SM the forward kernels are compiled for (register budget).
 #ifndef XLB_MINB_Q19_16
 #define XLB_MINB_Q19_16 9
@@ -42,34 +56,222 @@ struct MinBlocks {
       (COLL == 2) ? 5 : (Q == 27 ? 8 : (Q == 19 ? (sizeof(S) == 2 ? XLB_MINB_Q19_16 : 9) : 12));
 };
 
-// Bulk pass of an update, one thread per cell: pull-stream + collide
-// (+ body force) of every cell as if periodic.  src holds post-collision
-// populations h_{t-1} with ghost values in the boundary cells, so the pull is
-// exact for every fluid cell; dst receives h_t = C(S_bc(h_{t-1})).  Boundary
-// cells get values nobody reads until k_boundary rewrites them; inlet /
-// outlet cells are recomputed there too.
-// FW: the lattice has FWALL face planes (their cells reverse instead of
-// colliding, and pulls from them are plain); the FW = false instance carries
-// none of that logic.
+// Face types, per axis, of the coordinates v - 1, v and v + 1 (periodic) of
+// a cell, from the types lo and hi of the boundary face planes at 0 and
+// n - 1 (0: no face).  Axes of extent 1 carry no faces.
+__device__ __forceinline__ void axis_face_types(int v, int n, int lo, int hi, int (&t)[3]) {
+  t[0] = (v == 1 ? lo : 0) | (v == 0 ? hi : 0);
+  t[1] = (v == 0 ? lo : 0) | (v == n - 1 ? hi : 0);
+  t[2] = (v == n - 1 ? lo : 0) | (v == n - 2 ? hi : 0);
+}
+
+// Faces around a cell, packed into one word: the per-axis face types (3 bits
+// each) of the coordinates v - 1, v, v + 1 on x, y and z, and flags:
+//   SKIP:  the cell lies in a y / z face row of a WALL / LID / EQ face and is
+//          a boundary cell itself: it holds no state, its slots take the
+//          ghost values its neighbours push (where such a face meets an FWALL
+//          plane the edge cell is FWALL and holds state; where it meets a
+//          WALL plane it is WALL);
+//   XN:    some source of the cell lies on an x-face plane;
+//   RN:    some source may lie in a skipped row (a y / z coordinate of the
+//          cell or its neighbours is on a face plane);
+//   FWALL: the cell lies on an FWALL face only (it reverses).
+// With these, a direction's source w = x - c_i of rule type t (the combined
+// face types of w's coordinates, 0 for fluid or FWALL) is pulled plainly
+// when t = 0 or w is skipped (it then holds the pushed ghost value), and by
+// the rule by coordinates otherwise (an x-face cell in an ordinary row).
+constexpr uint32_t FC_SKIP = 1u << 27, FC_XN = 1u << 28, FC_RN = 1u << 29, FC_FWALL = 1u << 30;
+
+__device__ __forceinline__ int fc_type(uint32_t fc, int axis, int k) { return (int)(fc >> (3 * (3 * axis + k))) & 7; }
+
+template <bool FW>
+__device__ __forceinline__ uint32_t face_code(const StepParams& p, int x, int y, int z) {
+  if (!p.has_faces) return 0u;
+  // a cell two or more planes away from every boundary plane has no face
+  // coordinate among its own and its neighbours'
+  if (x > 1 && x < p.nx - 2 && y > 1 && y < p.ny - 2 && (p.nz == 1 || (z > 1 && z < p.nz - 2))) return 0u;
+  int tx[3], ty[3], tz[3];
+  axis_face_types(x, p.nx, p.face[0], p.face[1], tx);
+  axis_face_types(y, p.ny, p.face[2], p.face[3], ty);
+  axis_face_types(z, p.nz, p.face[4], p.face[5], tz);
+  uint32_t fc = 0u;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    fc |= (uint32_t)tx[k] << (3 * k) | (uint32_t)ty[k] << (3 * (3 + k)) | (uint32_t)tz[k] << (3 * (6 + k));
+  // x-face sources matter to cells that hold state: not to the boundary
+  // cells of an x-face plane themselves (FWALL ones do hold state)
+  if ((tx[0] | tx[2]) != 0 && (tx[1] == 0 || (FW && tx[1] == FWALL))) fc |= FC_XN;
+  if ((ty[0] | ty[1] | ty[2] | tz[0] | tz[1] | tz[2]) != 0) fc |= FC_RN;
+  const int self = face_combine<FW>(tx[1], ty[1], tz[1]);
+  if (self != 0 && face_combine<FW>(0, ty[1], tz[1]) != 0)
+    fc |= FC_SKIP;
+  else if (FW && self == 0 && (tx[1] == FWALL || ty[1] == FWALL || tz[1] == FWALL))
+    fc |= FC_FWALL;
+  return fc;
+}
+
+// Rule type of direction i's source and whether that source is a skipped
+// cell (its slot then holds the pushed ghost value).
+template <int Q, bool FW>
+__device__ __forceinline__ int source_rule(uint32_t fc, int i, bool& skipped) {
+  const int ry = fc_type(fc, 1, 1 - Lattice<Q>::c(i, 1)), rz = fc_type(fc, 2, 1 - Lattice<Q>::c(i, 2));
+  const int t = face_combine<FW>(fc_type(fc, 0, 1 - Lattice<Q>::c(i, 0)), ry, rz);
+  skipped = t != 0 && face_combine<FW>(0, ry, rz) != 0;
+  return t;
+}
+
+// Rules by coordinates for the sources on x-face planes in ordinary rows
+// (after a plain pull of the cell): WALL: h_opp(i)(x);  LID: h_opp(i)(x) +
+// 2 w_i rho_w (c_i . u_w) / cs^2;  EQ: f_i^eq(rho_w, u_w).
+template <int Q, typename S, bool FW>
+__device__ __forceinline__ void x_face_rules(const S* __restrict__ src, const StepParams& p, int self, uint32_t fc,
+                                             float (&df)[Q]) {
+  if (!(fc & FC_RN)) {
+    // an ordinary row: the source's type is the x-face's alone, one per side
+    const int tm = face_combine<FW>(fc_type(fc, 0, 0), 0, 0), tp = face_combine<FW>(fc_type(fc, 0, 2), 0, 0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      if (Lattice<Q>::c(i, 0) == 0) continue;
+      const int t = Lattice<Q>::c(i, 0) > 0 ? tm : tp;
+      if (t == 0) continue;
+      if (t == EQ)
+        df[i] = p.eq_df[i];
+      else
+        df[i] = Store<S>::ld(src + (long long)opposite<Q>(i) * p.plane + self) + (t == LID ? p.lid_term[i] : 0.f);
+    }
+    return;
+  }
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    if (Lattice<Q>::c(i, 0) == 0) continue;
+    bool skipped;
+    const int t = source_rule<Q, FW>(fc, i, skipped);
+    if (t == 0 || skipped) continue;
+    if (t == EQ)
+      df[i] = p.eq_df[i];
+    else
+      df[i] = Store<S>::ld(src + (long long)opposite<Q>(i) * p.plane + self) + (t == LID ? p.lid_term[i] : 0.f);
+  }
+}
+
+// Ghost values for the skipped neighbours of a cell x that holds state: for
+// each direction i whose source w = x - c_i is skipped, the value the rule
+// gives f_i(x) at the next pull goes into w's slot i (WALL: h_opp(i)(x) as
+// stored; LID: that + 2 w_i rho_w (c_i . u_w) / cs^2; EQ: f_i^eq(rho_w, u_w)).
+// df: the cell's post-collision values, rnd: how they are rounded into
+// storage.  (w, i) determines x, so no two cells write the same slot.
+template <int Q, typename S, bool FW>
+__device__ __forceinline__ void push_ghosts(S* __restrict__ dst, const StepParams& p, int x, int y, int z,
+                                            uint32_t fc, const float (&df)[Q], const CellRound<S>& rnd) {
+  Nbr nb;
+  make_nbr(nb, x, y, z, p.nx, p.ny, p.nz);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    bool skipped;
+    const int t = source_rule<Q, FW>(fc, i, skipped);
+    if (!skipped) continue;
+    const int o = opposite<Q>(i);
+    float v = p.eq_df[i];
+    if (t != EQ) v = rnd.rounded(o, df[o]) + (t == LID ? p.lid_term[i] : 0.f);
+    const long long slot = (long long)i * p.plane + src_index<Q>(nb, i);
+    st_ghost<S>(dst + slot, (uint32_t)slot, v);
+  }
+}
+
+// Plain periodic pull df_i(x) = h_i(x - c_i) of all Q populations, walking
+// the planes with one pointer (a 64-bit add per plane; a product i * plane
+// per direction costs more instructions).
+template <int Q, typename S>
+__device__ __forceinline__ void pull_plain(const S* __restrict__ src, const StepParams& p, const Nbr& nb,
+                                           float (&df)[Q]) {
+  const S* base = src;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    df[i] = Store<S>::ld(base + src_index<Q>(nb, i));
+    base += p.plane;
+  }
+}
+
+template <int Q, typename S>
+__device__ __forceinline__ void store_cell(S* __restrict__ dst, const StepParams& p, int self, const CellRound<S>& rnd,
+                                           const float (&df)[Q]) {
+  S* out = dst + self;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    rnd.st(out, i, df[i]);
+    out += p.plane;
+  }
+}
+
+// Which mechanism delivers the rules of the boundary faces to the bulk pass:
+// with 16-bit storage the cells of y / z face rows are skipped and take
+// ghost values pushed by the rows next to them, and only the sources on
+// x-face planes take the rule inside the pull (the kernel is bound by
+// instruction issue: whole warps skip or push, and only the lanes at the ends
+// of a row run face logic); FP32 applies every face rule by coordinates
+// inside the pull (the kernel is bound by memory traffic, and the face logic
+// hides under it).  Both give the same pulled values; the readouts, the
+// boundary pass and the adjoint apply the face rules by coordinates and never
+// read face cells.
+template <typename S>
+struct GhostFaces {
+  static constexpr bool value = sizeof(S) == 2;
+};
+
+// Bulk pass of an update, one thread per cell: pull + collide (+ body force)
+// + store.  src holds post-collision populations h_{t-1} whose boundary cells
+// carry ghost values (the rule's value for the pulling neighbour), so the
+// pull is exact for every cell that holds state; dst receives
+// h_t = C(S_bc(h_{t-1})).  Faces (whole boundary planes of one type) as
+// GhostFaces describes; cells on FWALL face planes reverse instead of
+// colliding (FW).  Other boundary cells get values nobody reads until
+// k_boundary rewrites them; inlet / outlet cells are recomputed there too.
 template <int Q, typename S, int COLL, bool FW>
 __global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, S, COLL>::value)
     k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, const StepParams p) {
   CellIdx c;
-  if (!cell_of_block(p, c)) return;
-  Nbr nb;
-  make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
+  if (!cell_of_grid(p, c)) return;
   float df[Q];
-  const bool on_fwall = pull_periodic<Q, S, FW>(src, p, nb, c.self, c.x, c.y, c.z, df);
-  if (FW && COLL != COLL_NONE && on_fwall)
+  uint32_t fc = 0u;
+  bool fwall = false;
+  if constexpr (GhostFaces<S>::value) {
+    fc = face_code<FW>(p, c.x, c.y, c.z);
+    if (fc & FC_SKIP) return;
+    Nbr nb;
+    make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
+    pull_plain<Q, S>(src, p, nb, df);
+    if (fc & FC_XN) x_face_rules<Q, S, FW>(src, p, c.self, fc, df);
+    fwall = (fc & FC_FWALL) != 0u;
+  } else {
+    Nbr nb;
+    make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
+    fwall = pull_periodic<Q, S, FW>(src, p, nb, c.self, c.x, c.y, c.z, df);
+  }
+  if (FW && COLL != COLL_NONE && fwall)
     reverse_populations<Q>(df);
   else
     collide<Q, COLL>(df, p);
-  S* out = dst + c.self;
+  CellRound<S> rnd;
+  rnd.begin((uint32_t)c.self, df);
+  if (GhostFaces<S>::value && (fc & FC_RN)) push_ghosts<Q, S, FW>(dst, p, c.x, c.y, c.z, fc, df, rnd);
+  store_cell<Q, S>(dst, p, c.self, rnd, df);
+}
+
+// Ghost values of a stored post-collision state (after a local collision or
+// a restored state), for storage types that use them: every cell next to a
+// skipped face cell pushes them from its stored values.
+template <int Q, typename S, bool FW>
+__global__ void __launch_bounds__(ROW_BLOCK) k_face_ghosts(S* f, const StepParams p) {
+  CellIdx c;
+  if (!cell_of_grid(p, c)) return;
+  const uint32_t fc = face_code<FW>(p, c.x, c.y, c.z);
+  if (!(fc & FC_RN) || (fc & FC_SKIP)) return;
+  float hs[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    Store<S>::st(out, df[i]);
-    out += p.plane;
-  }
+  for (int i = 0; i < Q; ++i) hs[i] = Store<S>::ld_plain(f + (long long)i * p.plane + c.self);
+  CellRound<S> rnd;  // the values are stored ones: rounding them again is exact
+  rnd.begin((uint32_t)c.self, hs);
+  push_ghosts<Q, S, FW>(f, p, c.x, c.y, c.z, fc, hs, rnd);
 }
 
 // Ghost value of the link (cell x, direction i) whose source w = x - c_i has
@@ -96,7 +298,8 @@ __device__ __forceinline__ void write_ghost(S* __restrict__ dst, const StepParam
   wy = wy < 0 ? p.ny - 1 : (wy >= p.ny ? 0 : wy);
   wz = wz < 0 ? p.nz - 1 : (wz >= p.nz ? 0 : wz);
   const float v = t == EQ ? eqv : (t == LID ? h_opp + add : h_opp);
-  Store<S>::st(dst + (long long)i * p.plane + (wx + p.nx * (wy + p.ny * wz)), v);
+  const long long slot = (long long)i * p.plane + (wx + p.nx * (wy + p.ny * wz));
+  st_ghost<S>(dst + slot, (uint32_t)slot, v);
 }
 
 // Ghost value of a WALL link with a Bouzidi wall distance q (Bouzidi,
@@ -199,10 +402,13 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ sr
     } else {
       collide<Q, COLL>(df, p);
     }
+    CellRound<S> rnd;
+    rnd.begin((uint32_t)self, df);
     S* out = dst + self;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      Store<S>::st(out, df[i]);
+      rnd.st(out, i, df[i]);
+      df[i] = rnd.rounded(i, df[i]);  // the stored value, as the link threads read it
       out += p.plane;
     }
   } else {
@@ -212,28 +418,25 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ sr
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const int t = __ldg(p.flags + src_index<Q>(nb, i)) & FLAG_TYPE;
-    if (!holds_state(t)) {
-      // the stored (rounded) value, as the link threads read it
-      S hs;
-      Store<S>::st(&hs, df[opposite<Q>(i)]);
-      write_ghost<Q, S>(dst, p, x, y, z, i, t, Store<S>::ld_plain(&hs));
-    }
+    if (!holds_state(t)) write_ghost<Q, S>(dst, p, x, y, z, i, t, df[opposite<Q>(i)]);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Vectorised direct kernel.  Each thread owns V consecutive cells of one row
+// Vectorised bulk kernel.  Each thread owns V consecutive cells of one row
 // (x0 = V * slot); a warp covers 32 V consecutive cells and never straddles a
 // row.  Every direction is one aligned V-wide load of the source row at x0;
 // the pull's x shift by c_x = +-1 takes the missing end element from the
 // neighbouring lane with a warp shuffle, and only the lane at the warp's (or
-// row's) edge loads it from memory, with the periodic wrap.  Like the one-cell
-// kernel it is a bulk pass (ghost values make the pull exact).  Stores are
-// V-wide.  Needs nx % V == 0.
+// row's) edge loads it from memory, with the periodic wrap.  Faces as for
+// the one-cell kernel with 16-bit storage: the rows of y / z faces are
+// skipped (whole warps) and receive ghost values from the rows next to
+// them; sources on x-face planes take the rule in the lanes at the ends of
+// a row.  Stores are V-wide.  Needs nx % V == 0; no FWALL faces.
 
 template <int Q, typename S, int COLL, int V>
 struct VecMinBlocks {
-  static constexpr int value = (COLL == 2) ? 5 : (Q * V > 64 ? 3 : 4);
+  static constexpr int value = (COLL == 2) ? 5 : (Q * V > 64 ? 3 : (Q * V > 32 ? 6 : 8));
 };
 
 template <int Q, typename S, int COLL, int V>
@@ -249,6 +452,14 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
   const bool active = slot * V < nx;
   const int x0 = active ? slot * V : nx - V;
   const int y = row % ny, z = row / ny;
+  // face types of the row's coordinates (uniform over the warp); a row on a
+  // WALL / LID / EQ face plane holds ghost values only
+  int ty[3] = {0, 0, 0}, tz[3] = {0, 0, 0};
+  if (p.has_faces) {
+    axis_face_types(y, ny, p.face[2], p.face[3], ty);
+    axis_face_types(z, nz, p.face[4], p.face[5], tz);
+    if (face_combine<false>(0, ty[1], tz[1]) != 0) return;  // the whole warp
+  }
   const bool last = !active || x0 + V >= nx;  // no active right neighbour lane
   const int xm = x0 == 0 ? nx - 1 : x0 - 1;    // element left of the vector
   const int xp = x0 + V >= nx ? 0 : x0 + V;    // element right of the vector
@@ -261,31 +472,6 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
 #pragma unroll
       for (int c = 0; c < 3; ++c) rb[b][c] = nx * (ys[b] + ny * zs[c]);
   }
-  // face types of the source coordinates (x0 + k -+ 1, y -+ 1, z -+ 1)
-  int tx[V][3], ty[3] = {0, 0, 0}, tz[3] = {0, 0, 0};
-  bool near = false;
-#pragma unroll
-  for (int k = 0; k < V; ++k) tx[k][0] = tx[k][1] = tx[k][2] = 0;
-  if (p.has_faces) {
-    const int fy0 = face_code(wrap_m(y, ny), ny), fy2 = face_code(wrap_p(y, ny), ny);
-    ty[0] = (fy0 & 1 ? p.face[2] : 0) | (fy0 & 2 ? p.face[3] : 0);
-    ty[2] = (fy2 & 1 ? p.face[2] : 0) | (fy2 & 2 ? p.face[3] : 0);
-    if (nz > 1) {
-      const int fz0 = face_code(wrap_m(z, nz), nz), fz2 = face_code(wrap_p(z, nz), nz);
-      tz[0] = (fz0 & 1 ? p.face[4] : 0) | (fz0 & 2 ? p.face[5] : 0);
-      tz[2] = (fz2 & 1 ? p.face[4] : 0) | (fz2 & 2 ? p.face[5] : 0);
-    }
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-      const int x = x0 + k;
-      const int fxm = face_code(x == 0 ? nx - 1 : x - 1, nx), fxp = face_code(x == nx - 1 ? 0 : x + 1, nx);
-      tx[k][0] = (fxm & 1 ? p.face[0] : 0) | (fxm & 2 ? p.face[1] : 0);
-      tx[k][2] = (fxp & 1 ? p.face[0] : 0) | (fxp & 2 ? p.face[1] : 0);
-      near |= (tx[k][0] | tx[k][2]) != 0;
-    }
-    near |= (ty[0] | ty[2] | tz[0] | tz[2]) != 0;
-  }
-  const int self0 = x0 + nx * row;
   float v[Q][V];
   const S* base = src;
 #pragma unroll
@@ -308,43 +494,68 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
 #pragma unroll
       for (int k = 0; k < V - 1; ++k) v[i][k] = w[k + 1];
     }
-    if (i > 0 && near) {
-      // sources on a boundary face read the own opposite population instead
-      // (lanes next to a face only; the loads join the same phase)
-      const S* own = src + (long long)opposite<Q>(i) * p.plane + self0;
-#pragma unroll
-      for (int k = 0; k < V; ++k) {
-        const int t = face_combine<false>(tx[k][1 - cx], ty[1 - Lattice<Q>::c(i, 1)], tz[1 - Lattice<Q>::c(i, 2)]);
-        if (t == WALL || t == LID) v[i][k] = Store<S>::ld(own + k);
-      }
-    }
     base += p.plane;
   }
-  if (near) {
+  const int self0 = x0 + nx * row;
+  // sources on x-face planes (only the lanes at the ends of a row have them)
+  if (p.has_faces && (x0 <= 1 || x0 + V >= nx - 1)) {
 #pragma unroll
-    for (int i = 1; i < Q; ++i)
+    for (int k = 0; k < V; ++k) {
+      int tx[3];
+      axis_face_types(x0 + k, nx, p.face[0], p.face[1], tx);
+      if ((tx[0] | tx[2]) == 0 || tx[1] != 0) continue;  // no x-face source, or an x-face cell itself
+      uint32_t fc = (ty[0] | ty[1] | ty[2] | tz[0] | tz[1] | tz[2]) != 0 ? FC_RN : 0u;
 #pragma unroll
-      for (int k = 0; k < V; ++k) {
-        const int t = face_combine<false>(tx[k][1 - Lattice<Q>::c(i, 0)], ty[1 - Lattice<Q>::c(i, 1)],
-                                          tz[1 - Lattice<Q>::c(i, 2)]);
-        if (t == EQ) v[i][k] = p.eq_df[i];
-        if (t == LID) v[i][k] += p.lid_term[i];
-      }
+      for (int a = 0; a < 3; ++a)
+        fc |= (uint32_t)tx[a] << (3 * a) | (uint32_t)ty[a] << (3 * (3 + a)) | (uint32_t)tz[a] << (3 * (6 + a));
+      float d[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) d[i] = v[i][k];
+      x_face_rules<Q, S, false>(src, p, self0 + k, fc, d);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) v[i][k] = d[i];
+    }
   }
+  CellRound<S> rnd[V];
 #pragma unroll
   for (int k = 0; k < V; ++k) {
     float d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = v[i][k];
     collide<Q, COLL>(d, p);
+    rnd[k].begin((uint32_t)(self0 + k), d);
 #pragma unroll
     for (int i = 0; i < Q; ++i) v[i][k] = d[i];
   }
   if (!active) return;
+  // ghost values for the skipped face rows next to this row (from registers,
+  // every lane of the row)
+  if (p.has_faces && (ty[0] | ty[2] | tz[0] | tz[2]) != 0) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      int tx[3];
+      axis_face_types(x0 + k, nx, p.face[0], p.face[1], tx);
+      uint32_t fc = FC_RN;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        fc |= (uint32_t)tx[a] << (3 * a) | (uint32_t)ty[a] << (3 * (3 + a)) | (uint32_t)tz[a] << (3 * (6 + a));
+      float d[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) d[i] = v[i][k];
+      push_ghosts<Q, S, false>(dst, p, x0 + k, y, z, fc, d, rnd[k]);
+    }
+  }
   S* out = dst + (long long)nx * row + x0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    VecIO<S, V>::st(out, v[i]);
+    if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+      uint16_t b[V];
+#pragma unroll
+      for (int k = 0; k < V; ++k) b[k] = rnd[k].bits(i, v[i][k]);
+      VecIO<S, V>::st_bits(out, b);
+    } else {
+      VecIO<S, V>::st(out, v[i]);
+    }
     out += p.plane;
   }
 }
@@ -364,8 +575,10 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_collide_local(S* f, const StepPar
     reverse_populations<Q>(df);
   else
     collide<Q, COLL>(df, p);
+  CellRound<S> rnd;
+  rnd.begin((uint32_t)c.self, df);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) Store<S>::st(f + (long long)i * p.plane + c.self, df[i]);
+  for (int i = 0; i < Q; ++i) rnd.st(f + (long long)i * p.plane + c.self, i, df[i]);
 }
 
 // f_0 = f^eq(rho, u) on fluid-like cells (Eq. 5); EQ cells take
@@ -397,8 +610,10 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_init(S* f, const StepParams p, co
 #pragma unroll
     for (int i = 0; i < Q; ++i) df[i] = 0.f;
   }
+  CellRound<S> rnd;
+  rnd.begin((uint32_t)c.self, df);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) Store<S>::st(f + (long long)i * p.plane + c.self, df[i]);
+  for (int i = 0; i < Q; ++i) rnd.st(f + (long long)i * p.plane + c.self, i, df[i]);
 }
 
 // Post-stream populations of a cell: pulled from h (state holds h) or read
@@ -416,90 +631,102 @@ __device__ __forceinline__ void post_stream(const S* f, const StepParams& p, con
   }
 }
 
-// Observables of the post-stream state (Eqs. 6-7): rho and the reported
-// velocity u = (j + F/2) / rho on fluid-like cells; EQ cells report
-// (rho_w, u_w); solid cells report zeros.  u is component-major, stride ucs.
-template <int Q, typename S>
-__global__ void __launch_bounds__(ROW_BLOCK) k_macroscopic(const S* f, const StepParams p, int kind_h,
-                                                           float* rho_out, float* u_out, long long ucs) {
-  CellIdx c;
-  if (!cell_of_block(p, c)) return;
-  const int fl = p.has_mask ? p.flags[c.self] : 0;
-  const int t = fl & FLAG_TYPE;
-  float rho = 0.f, u[3] = {0.f, 0.f, 0.f};
-  if (fluid_like(t)) {
-    float df[Q];
-    post_stream<Q, S>(f, p, c, fl, kind_h, df);
-    float drho, j[3];
-    moments<Q>(df, drho, j);
-    if (p.has_force) {
-      j[0] += 0.5f * p.F[0];
-      j[1] += 0.5f * p.F[1];
-      j[2] += 0.5f * p.F[2];
-    }
-    rho = 1.0f + drho;
-    u[0] = j[0] / rho;
-    u[1] = j[1] / rho;
-    u[2] = j[2] / rho;
-  } else if (t == EQ) {
-    rho = p.eq_rho;
-    u[0] = p.eq_u[0];
-    u[1] = p.eq_u[1];
-    u[2] = p.eq_u[2];
-  }
-  if (rho_out) rho_out[c.self] = rho;
-  if (u_out) {
-    u_out[c.self] = u[0];
-    u_out[ucs + c.self] = u[1];
-    if (Lattice<Q>::D == 3) u_out[2 * ucs + c.self] = u[2];
-  }
-}
+// Readouts of the post-stream state, one kernel for the three of them (so
+// that the boundary-aware pull is compiled once per lattice and storage):
+//  RD_MACRO:   observables (Eqs. 6-7): rho and the reported velocity
+//              u = (j + F/2) / rho on fluid-like cells; EQ cells report
+//              (rho_w, u_w); solid cells zeros.  u is component-major, stride ucs.
+//  RD_MOMENTS: FP64 block partial sums of (mass, j_x, j_y, j_z) over the
+//              fluid-like cells (populations w_i + df_i, bare momentum).
+//  RD_KE:      FP64 block partial sums of the kinetic energy (1/2) rho |u|^2
+//              of the observables RD_MACRO reports (rho, u formed in FP32, the
+//              square and the sum in FP64): the loss of the gradient
+//              workloads (Section 6 takes gradients of rollout losses).
+// Grid-stride over the cells of the box [lo, lo + ext); one partial row
+// (4 doubles) per block for the sums.
+enum ReadoutMode { RD_MACRO = 0, RD_MOMENTS = 1, RD_KE = 2 };
 
-// Block-level FP64 partial sums of (mass, j_x, j_y, j_z) over fluid-like
-// cells of the post-stream state; one row of 4 doubles per block.
 template <int Q, typename S>
-__global__ void __launch_bounds__(ROW_BLOCK) k_reduce_partial(const S* f, const StepParams p, int kind_h,
-                                                              double* partial) {
-  CellIdx c;
+__global__ void __launch_bounds__(ROW_BLOCK) k_readout(const S* f, const StepParams p, int kind_h, int mode,
+                                                       int3 lo, int3 ext, float* rho_out, float* u_out,
+                                                       long long ucs, double* partial) {
+  const long long nbox = (long long)ext.x * ext.y * ext.z;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  if (cell_of_block(p, c)) {
+  for (long long k = blockIdx.x * (long long)ROW_BLOCK + threadIdx.x; k < nbox;
+       k += (long long)gridDim.x * ROW_BLOCK) {
+    CellIdx c;
+    const long long r = k / ext.x;
+    c.x = lo.x + (int)(k - r * ext.x);
+    c.y = lo.y + (int)(r % ext.y);
+    c.z = lo.z + (int)(r / ext.y);
+    c.self = c.x + p.nx * (c.y + p.ny * c.z);
     const int fl = p.has_mask ? p.flags[c.self] : 0;
-    if (fluid_like(fl & FLAG_TYPE)) {
+    const int t = fl & FLAG_TYPE;
+    float rho = 0.f, u[3] = {0.f, 0.f, 0.f};
+    if (fluid_like(t)) {
       float df[Q];
       post_stream<Q, S>(f, p, c, fl, kind_h, df);
-      // FP64 accumulation of the cell's moments (the populations are w_i + df_i)
-      double m = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+      if (mode == RD_MOMENTS) {
+        double m = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const double fi = weight_d<Q>(i) + (double)df[i];
-        m += fi;
-        jx += Lattice<Q>::c(i, 0) * fi;
-        jy += Lattice<Q>::c(i, 1) * fi;
-        jz += Lattice<Q>::c(i, 2) * fi;
+        for (int i = 0; i < Q; ++i) {
+          const double fi = weight_d<Q>(i) + (double)df[i];
+          m += fi;
+          jx += Lattice<Q>::c(i, 0) * fi;
+          jy += Lattice<Q>::c(i, 1) * fi;
+          jz += Lattice<Q>::c(i, 2) * fi;
+        }
+        acc[0] += m;
+        acc[1] += jx;
+        acc[2] += jy;
+        acc[3] += jz;
+        continue;
       }
-      acc[0] = m;
-      acc[1] = jx;
-      acc[2] = jy;
-      acc[3] = jz;
+      float drho, j[3];
+      moments<Q>(df, drho, j);
+      if (p.has_force) {
+        j[0] += 0.5f * p.F[0];
+        j[1] += 0.5f * p.F[1];
+        j[2] += 0.5f * p.F[2];
+      }
+      rho = 1.0f + drho;
+      u[0] = j[0] / rho;
+      u[1] = j[1] / rho;
+      u[2] = Lattice<Q>::D == 3 ? j[2] / rho : 0.f;
+    } else if (t == EQ) {
+      rho = p.eq_rho;
+      u[0] = p.eq_u[0];
+      u[1] = p.eq_u[1];
+      u[2] = Lattice<Q>::D == 3 ? p.eq_u[2] : 0.f;
+    }
+    if (mode == RD_KE) {
+      const double u0 = u[0], u1 = u[1], u2 = u[2];
+      acc[0] += 0.5 * (double)rho * (u0 * u0 + u1 * u1 + u2 * u2);
+    } else if (mode == RD_MACRO) {
+      if (rho_out) rho_out[c.self] = rho;
+      if (u_out) {
+        u_out[c.self] = u[0];
+        u_out[ucs + c.self] = u[1];
+        if (Lattice<Q>::D == 3) u_out[2 * ucs + c.self] = u[2];
+      }
     }
   }
+  if (mode == RD_MACRO) return;
   __shared__ double red[ROW_BLOCK / 32][4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k)
+  for (int m = 0; m < 4; ++m)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
-  const int w = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_down_sync(0xffffffffu, acc[m], o);
   if ((threadIdx.x & 31) == 0)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) red[w][k] = acc[k];
+    for (int m = 0; m < 4; ++m) red[threadIdx.x >> 5][m] = acc[m];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < 4; ++k) {
+  if (threadIdx.x == 0)
+    for (int m = 0; m < 4; ++m) {
       double s = 0.0;
-      for (int q = 0; q < ROW_BLOCK / 32; ++q) s += red[q][k];
-      partial[4 * (long long)blockIdx.x + k] = s;
+      for (int q = 0; q < ROW_BLOCK / 32; ++q) s += red[q][m];
+      partial[4 * (long long)blockIdx.x + m] = s;
     }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -580,22 +807,44 @@ int launch_typed(Op op, const LaunchArgs& a) {
   cudaStream_t st = (cudaStream_t)a.stream;
   switch (op) {
     case OP_STEP:
-      if (p.face[0] == FWALL || p.face[1] == FWALL || p.face[2] == FWALL || p.face[3] == FWALL ||
-          p.face[4] == FWALL || p.face[5] == FWALL)
-        k_stream_collide<Q, S, COLL, true><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, p);
+    case OP_FACE_GHOSTS: {
+      // bulk kernels run on an (x-blocks, ny, nz) grid where it fits
+      StepParams q = p;
+      dim3 g3 = grid;
+      if (p.ny <= 65535 && p.nz <= 65535) {
+        q.grid3 = 1;
+        g3 = dim3((unsigned)nxb, (unsigned)p.ny, (unsigned)p.nz);
+      }
+      const bool fw = p.face[0] == FWALL || p.face[1] == FWALL || p.face[2] == FWALL || p.face[3] == FWALL ||
+                      p.face[4] == FWALL || p.face[5] == FWALL;
+      if (op == OP_FACE_GHOSTS) {
+        if (!p.has_faces || !GhostFaces<S>::value) return 0;
+        if (fw)
+          k_face_ghosts<Q, S, true><<<g3, block, 0, st>>>((S*)a.dst, q);
+        else
+          k_face_ghosts<Q, S, false><<<g3, block, 0, st>>>((S*)a.dst, q);
+        return 0;
+      }
+      if (fw)
+        k_stream_collide<Q, S, COLL, true><<<g3, block, 0, st>>>((const S*)a.src, (S*)a.dst, q);
       else
-        k_stream_collide<Q, S, COLL, false><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, p);
+        k_stream_collide<Q, S, COLL, false><<<g3, block, 0, st>>>((const S*)a.src, (S*)a.dst, q);
       return 0;
+    }
     case OP_STEP_VEC: {
-      // 16-bit storage, BGK / NONE, D2Q9 / D3Q19 only (FP32 is faster with one
-      // cell per thread; on D3Q27 the 4 x 27 live values do not pay), V = 4
-      constexpr int V = 4;
-      if constexpr (sizeof(S) == 2 && Q != 27 && COLL != COLL_KBC) {
+      // 16-bit storage, BGK, D2Q9 / D3Q19 only (FP32 is faster with one cell
+      // per thread; on D3Q27 the V x 27 live values do not pay); V = 4
+      // (8-byte words) or 2 (4-byte words)
+      if constexpr (sizeof(S) == 2 && Q != 27 && COLL == COLL_BGK) {
+        const int V = a.vec_width == 2 ? 2 : 4;
         if (p.nx % V != 0) return -7;
         const long long spr = (p.nx / V + 31) / 32 * 32;
         const long long blocks = (spr * p.ny * p.nz + 127) / 128;
         if (blocks > 0x7fffffffLL) return -1;
-        k_sc_vec<Q, S, COLL, V><<<(unsigned)blocks, 128, 0, st>>>((const S*)a.src, (S*)a.dst, p);
+        if (V == 2)
+          k_sc_vec<Q, S, COLL, 2><<<(unsigned)blocks, 128, 0, st>>>((const S*)a.src, (S*)a.dst, p);
+        else
+          k_sc_vec<Q, S, COLL, 4><<<(unsigned)blocks, 128, 0, st>>>((const S*)a.src, (S*)a.dst, p);
         return 0;
       }
       return -7;
@@ -621,12 +870,23 @@ int launch_typed(Op op, const LaunchArgs& a) {
         k_init<Q, S><<<grid, block, 0, st>>>((S*)a.dst, p, a.rho, a.u, a.ucs);
         return 0;
       case OP_MACRO:
-        k_macroscopic<Q, S><<<grid, block, 0, st>>>((const S*)a.src, p, a.kind_h, a.rho_out, a.u_out, a.ucs);
-        return 0;
       case OP_REDUCE_PARTIAL:
-        if (a.partial_capacity < nblk) return -3;
-        k_reduce_partial<Q, S><<<grid, block, 0, st>>>((const S*)a.src, p, a.kind_h, a.partial);
+      case OP_KE_PARTIAL: {
+        // readouts over a box: the whole lattice, or the KE box; the sums take
+        // min(ceil(box cells / ROW_BLOCK), partial_capacity) blocks, at least 1
+        const bool box = op == OP_KE_PARTIAL;
+        const int3 lo = box ? make_int3(a.box_lo[0], a.box_lo[1], a.box_lo[2]) : make_int3(0, 0, 0);
+        const int3 ext = box ? make_int3(a.box_ext[0], a.box_ext[1], a.box_ext[2]) : make_int3(p.nx, p.ny, p.nz);
+        const long long nbox = (long long)ext.x * ext.y * ext.z;
+        long long b = (nbox + ROW_BLOCK - 1) / ROW_BLOCK;
+        if (op != OP_MACRO && b > a.partial_capacity) b = a.partial_capacity;
+        if (b > 0x7fffffffLL) b = 0x7fffffffLL;
+        if (b < 1) b = 1;
+        const int mode = op == OP_MACRO ? RD_MACRO : (op == OP_REDUCE_PARTIAL ? RD_MOMENTS : RD_KE);
+        k_readout<Q, S><<<(unsigned)b, ROW_BLOCK, 0, st>>>((const S*)a.src, p, a.kind_h, mode, lo, ext, a.rho_out,
+                                                          a.u_out, a.ucs, a.partial);
         return 0;
+      }
       case OP_WALL_FORCE: {
         // blocks: one per 256 links, at most the rows the partial buffer holds
         long long b = (a.n_links + 255) / 256;

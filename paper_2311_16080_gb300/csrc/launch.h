@@ -16,8 +16,11 @@ enum Op {
   OP_REDUCE_PARTIAL = 4, // block partial sums of mass and momentum
   OP_STEP_VEC = 7,       // fused stream + collide, V cells per thread, vector loads
   OP_BOUNDARY = 8,       // ghost values of the boundary links + fix-up cell recompute
-  OP_WALL_FORCE = 9      // block partial sums of the momentum-exchange force:
+  OP_WALL_FORCE = 9,     // block partial sums of the momentum-exchange force:
                          // min(ceil(n_links / 256), partial_capacity) rows, at least 1
+  OP_KE_PARTIAL = 10,    // block partial sums of the kinetic energy over a box:
+                         // min(ceil(box cells / ROW_BLOCK), partial_capacity) rows, at least 1
+  OP_FACE_GHOSTS = 11    // ghost values of the boundary faces from the stored state in dst
 };
 
 struct LaunchArgs {
@@ -40,6 +43,8 @@ struct LaunchArgs {
   const int* fix;              // OP_BOUNDARY fix-up cells (INLET, OUTLET, FWALL off the faces)
   long long n_fix;
   int recompute;               // OP_BOUNDARY: recompute the fix-up cells from src
+  int box_lo[3], box_ext[3];   // OP_KE_PARTIAL: first cell and extent of the box per axis
+  int vec_width;               // OP_STEP_VEC: cells per thread (2 or 4)
   void* stream;
 };
 
@@ -57,6 +62,9 @@ long long row_blocks(const StepParams& p);
 int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int ny, int nz, int* err_word,
                         void* stream);
 int launch_reduce_final(const double* partial, long long n, double* out, void* stream);
+// FP64 sum of squares of n floats (device memory) into column 0 of
+// min(ceil(n / 2048), capacity) partial rows (at least 1); returns the rows used.
+long long launch_sum_squares(const float* x, long long n, double* partial, long long capacity, void* stream);
 
 // Boundary tables of a mask by compaction: mode 0 selects the FLUID cells
 // (and FWALL cells of FWALL faces) whose source in direction `dir` is WALL /

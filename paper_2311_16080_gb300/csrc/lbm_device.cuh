@@ -169,11 +169,11 @@ __device__ __forceinline__ bool pull_periodic(const S* __restrict__ src, const S
   return FW && (fcx[1] == FWALL || fcy[1] == FWALL || fcz[1] == FWALL);
 }
 
-// Zou-He velocity inlet (inflow along +x; unknown populations have c_x = +1):
-//   rho = [sum_{c_x=0} f_i + 2 sum_{c_x=-1} f_i] / (1 - u_x),
-//   f_i = f_opp(i) + f_i^eq - f_opp(i)^eq = f_opp(i) + 6 w_i rho (c_i . u).
-// In deviations the rest parts of the numerator sum to exactly 1.
-// The inlet velocity is StepParams::inlet_u, or the cell's entry of
+// Velocity boundaries at INLET cells, with inward normal n = sign e_axis
+// (StepParams::inlet_axis / inlet_sign; +x, an inflow, by default; with a
+// velocity parallel to the wall they are a moving wall).  The unknown
+// populations are those entering the fluid through the boundary, c_i.n = +1.
+// The velocity is StepParams::inlet_u, or the cell's entry of
 // StepParams::inlet_field (a velocity profile) when that is set.
 template <int Q>
 __device__ __forceinline__ void inlet_velocity(const StepParams& p, int self, float (&u)[3]) {
@@ -188,20 +188,37 @@ __device__ __forceinline__ void inlet_velocity(const StepParams& p, int self, fl
   }
 }
 
+// c_i . n for the inlet normal
+template <int Q>
+__device__ __forceinline__ int inlet_cn(const StepParams& p, int i) {
+  const int c = p.inlet_axis == 0 ? Lattice<Q>::c(i, 0) : (p.inlet_axis == 1 ? Lattice<Q>::c(i, 1) : Lattice<Q>::c(i, 2));
+  return p.inlet_sign * c;
+}
+
+// rho = [sum_{c.n=0} f_i + 2 sum_{c.n=-1} f_i] / (1 - u.n); in deviations the
+// rest parts of the numerator sum to exactly 1.
+template <int Q>
+__device__ __forceinline__ float inlet_density(const StepParams& p, const float (&df)[Q], const float (&u)[3]) {
+  float s = 1.0f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cn = inlet_cn<Q>(p, i);
+    if (cn == 0) s += df[i];
+    if (cn == -1) s += 2.0f * df[i];
+  }
+  const float un = p.inlet_sign * (p.inlet_axis == 0 ? u[0] : (p.inlet_axis == 1 ? u[1] : u[2]));
+  return s / (1.0f - un);
+}
+
+// Zou-He: each unknown f_i = f_opp(i) + f_i^eq - f_opp(i)^eq = f_opp(i) + 6 w_i rho (c_i . u).
 template <int Q>
 __device__ __forceinline__ void zou_he_inlet(const StepParams& p, int self, float (&df)[Q]) {
   float u[3];
   inlet_velocity<Q>(p, self, u);
-  float s = 1.0f;
+  const float rho = inlet_density<Q>(p, df, u);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    if (Lattice<Q>::c(i, 0) == 0) s += df[i];
-    if (Lattice<Q>::c(i, 0) == -1) s += 2.0f * df[i];
-  }
-  const float rho = s / (1.0f - u[0]);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (Lattice<Q>::c(i, 0) == 1) {
+    if (inlet_cn<Q>(p, i) == 1) {
       float cu = Lattice<Q>::c(i, 0) * u[0] + Lattice<Q>::c(i, 1) * u[1];
       if (Lattice<Q>::D == 3) cu += Lattice<Q>::c(i, 2) * u[2];
       df[i] = df[opposite<Q>(i)] + 6.0f * weight<Q>(i) * rho * cu;
@@ -209,22 +226,16 @@ __device__ __forceinline__ void zou_he_inlet(const StepParams& p, int self, floa
   }
 }
 
-// Regularized velocity inlet (Latt et al. 2008, the other inflow rule
-// Section 4.3 names): rho as for Zou-He; non-equilibrium parts of the known
-// populations, those of the unknown (c_x = +1) ones by bounce-back;
-// Pi = sum_i c_i c_i f^neq_i; every population becomes
-//   f_i = f_i^eq(rho, u) + w_i / (2 cs^4) (c_i c_i - cs^2 I) : Pi.
+// Regularized velocity boundary (Latt et al. 2008; the other inflow rule
+// Section 4.3 names, and the regularized lid of Section 4.2): rho as for
+// Zou-He; non-equilibrium parts of the known populations, those of the
+// unknown ones by bounce-back; Pi = sum_i c_i c_i f^neq_i; every population
+// becomes f_i = f_i^eq(rho, u) + w_i / (2 cs^4) (c_i c_i - cs^2 I) : Pi.
 template <int Q>
 __device__ __forceinline__ void regularized_inlet(const StepParams& p, int self, float (&df)[Q]) {
   float u[3];
   inlet_velocity<Q>(p, self, u);
-  float s = 1.0f;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (Lattice<Q>::c(i, 0) == 0) s += df[i];
-    if (Lattice<Q>::c(i, 0) == -1) s += 2.0f * df[i];
-  }
-  const float rho = s / (1.0f - u[0]);
+  const float rho = inlet_density<Q>(p, df, u);
   const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   // equilibrium deviations f_i^eq - w_i, then the non-equilibrium parts
 #pragma unroll
@@ -234,7 +245,7 @@ __device__ __forceinline__ void regularized_inlet(const StepParams& p, int self,
   }
 #pragma unroll
   for (int i = 0; i < Q; ++i)
-    if (Lattice<Q>::c(i, 0) == 1) df[i] = df[opposite<Q>(i)];
+    if (inlet_cn<Q>(p, i) == 1) df[i] = df[opposite<Q>(i)];
   float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {

@@ -215,6 +215,38 @@ __global__ void k_reduce_final(const double* __restrict__ partial, long long n, 
   if (threadIdx.x < 4) out[threadIdx.x] = s[threadIdx.x][0];
 }
 
+// FP64 sum of squares of n floats (the gradient norm of the differentiable
+// workloads); grid-stride, one row (sum, 0, 0, 0) per block.
+__global__ void k_sum_squares_partial(const float* __restrict__ x, long long n, double* partial) {
+  double acc = 0.0;
+  for (long long k = blockIdx.x * 256LL + threadIdx.x; k < n; k += (long long)gridDim.x * 256) {
+    const double v = x[k];
+    acc += v * v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < 8; ++q) s += red[q];
+    partial[4 * (long long)blockIdx.x] = s;
+    partial[4 * (long long)blockIdx.x + 1] = 0.0;
+    partial[4 * (long long)blockIdx.x + 2] = 0.0;
+    partial[4 * (long long)blockIdx.x + 3] = 0.0;
+  }
+}
+
+long long launch_sum_squares(const float* x, long long n, double* partial, long long capacity, void* stream) {
+  long long b = (n + 2047) / 2048;
+  if (b > capacity) b = capacity;
+  if (b > 65535) b = 65535;
+  if (b < 1) b = 1;
+  k_sum_squares_partial<<<(unsigned)b, 256, 0, (cudaStream_t)stream>>>(x, n, partial);
+  return b;
+}
+
 int launch_reduce_final(const double* partial, long long n, double* out, void* stream) {
   k_reduce_final<<<1, 256, 0, (cudaStream_t)stream>>>(partial, n, out);
   return 0;

@@ -1,13 +1,15 @@
 // Allocation-free variant of the FP64 mass / momentum reduction.
 //
-// Who needs it: code that must not call cudaMalloc -- for example a caller
-// running inside a CUDA graph it is capturing or replaying, a real-time loop
-// that has pre-allocated everything and must not hit the allocator (whose
-// calls can synchronise the device), or a host framework that owns all device
-// memory through its own pool.  xlb_reduce keeps its block partial sums in a
-// buffer that each simulation context allocates; this entry point instead
-// keeps them in one fixed array compiled into the library, so a call touches
-// only memory that already exists.
+// Who needs it: callers that cannot call cudaMalloc.  A latency-critical
+// loop cannot afford it, because the allocator may synchronise the device and
+// takes unbounded time.  A host framework that owns all device memory through
+// its own pool allocator, under a fixed memory budget, forbids allocations
+// made behind its back.  A recovery path that runs after the device has
+// already run out of memory still needs the totals to report the state.
+// xlb_reduce keeps its block partial sums in a buffer that each simulation
+// context allocates; this entry point instead keeps them in one fixed array
+// compiled into the library, so a call touches only memory that already
+// exists.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds it (128 KiB) until the process exits.  All calls on a device
@@ -15,6 +17,13 @@
 // different host threads without ordering) race on it; order them on one
 // stream.  Each call writes every partial row it reads, so nothing has to be
 // cleared between calls.
+//
+// The call sums the populations as they are stored.  After xlb_step the live
+// buffer of a simulation holds the post-collision state h_{t-1} (the pull of
+// the next update streams it), not the post-stream state f_t that
+// xlb_reduce sums; on a periodic lattice without a body force the totals of
+// the two agree (collision and streaming conserve mass and momentum), on a
+// lattice with walls, inlets or a moving lid they differ.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -116,10 +125,10 @@ extern "C" int xlb_moments_noalloc(int lattice, const int64_t dims[3], int stora
   if (storage < XLB_STORE_F32 || storage > XLB_STORE_BF16) return XLB_ERR_ARG;
   const long long nx = dims[0], ny = dims[1], nz = dims[2];
   if (nx < 1 || ny < 1 || nz < 1 || (lattice == 9 && nz != 1)) return XLB_ERR_ARG;
-  if (nx > NA_MAX_CELLS || ny > NA_MAX_CELLS || nz > NA_MAX_CELLS) return XLB_ERR_ARG;
+  // the fixed scratch holds 4096 partial rows of 16384 cells each; the
+  // product is checked factor by factor so that it cannot overflow
+  if (nx > NA_MAX_CELLS || ny > NA_MAX_CELLS / nx || nz > NA_MAX_CELLS / (nx * ny)) return XLB_ERR_ARG;
   const long long n = nx * ny * nz;
-  // the fixed scratch holds 4096 partial rows of 16384 cells each
-  if (n > NA_MAX_CELLS) return XLB_ERR_ARG;
   if (plane_stride < n) return XLB_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return XLB_ERR_CUDA;
@@ -145,6 +154,16 @@ extern "C" int xlb_moments_noalloc(int lattice, const int64_t dims[3], int stora
   else
     cudaGetLastError();
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!out_on_device) {
+    // a host result needs a copy and a synchronisation of the stream, which
+    // a stream that is being captured does not allow
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return XLB_ERR_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return XLB_ERR_ARG;
+  }
   const int nb = (int)((n + NA_CELLS_PER_BLOCK - 1) / NA_CELLS_PER_BLOCK);
   double* result = scratch + 4 * NA_MAX_PARTIALS;
   const int Q = lattice;

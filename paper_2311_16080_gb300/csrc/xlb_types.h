@@ -45,6 +45,7 @@ struct StepParams {
   float inlet_u[3];      // Zou-He inlet velocity
   const float* inlet_field;  // or per-cell inlet velocities (D x N, component-major), or null
   int inlet_regularized;     // INLET rule: 0 Zou-He, 1 regularized
+  int inlet_axis, inlet_sign;  // inward normal n = sign e_axis of the INLET boundary
   int* err;              // device error word for kernels with bounded waits
   // Boundary faces: type (0 = none, WALL, LID, EQ or FWALL) of each whole
   // face plane x = 0, x = nx-1, y = 0, y = ny-1, z = 0, z = nz-1 that the
@@ -54,6 +55,9 @@ struct StepParams {
   // colliding; every other WALL / LID / EQ source uses ghost values.
   int face[6];
   int has_faces;
+  // bulk kernels: 1 when launched on a (x-blocks, ny, nz) grid, 0 when the
+  // grid is flattened over rows (ny or nz above the grid limit)
+  int grid3;
 };
 
 // Ghost link entries are int2 {cell, dir | type << 8 | flags << 16}; LINK_BZ

@@ -8,7 +8,8 @@ if the library is missing, loading raises instead of falling back to any
 CPU implementation.
 
 ``Simulation`` is a small convenience wrapper over one ctx, and
-``KineticEnergyRollout`` / ``rollout`` expose the adjoint to torch autograd.
+``KineticEnergyRollout()`` (the torch.autograd.Function class) / ``rollout``
+expose the adjoint to torch autograd.
 """
 from __future__ import annotations
 
@@ -24,7 +25,7 @@ XLB_OK, XLB_ERR_ARG, XLB_ERR_UNSUPPORTED, XLB_ERR_OOM, XLB_ERR_CUDA, XLB_ERR_TIM
 XLB_D2Q9, XLB_D3Q19, XLB_D3Q27 = 9, 19, 27
 XLB_COLL_NONE, XLB_COLL_BGK, XLB_COLL_KBC = 0, 1, 2
 XLB_STORE_F32, XLB_STORE_F16, XLB_STORE_BF16 = 0, 1, 2
-XLB_KERNEL_AUTO, XLB_KERNEL_DIRECT, XLB_KERNEL_VEC = 0, 1, 2
+XLB_KERNEL_AUTO, XLB_KERNEL_DIRECT, XLB_KERNEL_VEC, XLB_KERNEL_VEC2 = 0, 1, 2, 3
 XLB_CELL_FLUID, XLB_CELL_WALL, XLB_CELL_LID, XLB_CELL_INLET, XLB_CELL_OUTLET, XLB_CELL_EQ, XLB_CELL_FWALL = range(7)
 XLB_INLET_ZOU_HE, XLB_INLET_REGULARIZED = 0, 1
 
@@ -58,6 +59,9 @@ _PROTOS = {
     "xlb_macroscopic": (_i, [_vp, _vp, _vp]),
     "xlb_reduce": (_i, [_vp, C.POINTER(_d), C.POINTER(_d)]),
     "xlb_synchronize": (_i, [_vp]),
+    "xlb_kinetic_energy": (_i, [_vp, C.POINTER(_i64), C.POINTER(_i64), _vp]),
+    "xlb_sum_squares": (_i, [_vp, _vp, _i64, _vp]),
+    "xlb_adjoint_seed_kinetic_energy": (_i, [_vp, C.POINTER(_i64), C.POINTER(_i64), _d]),
     "xlb_moments_noalloc": (_i, [_i, C.POINTER(_i64), _i, _vp, _i64, _vp, _vp, _vp]),
     "xlb_state_bytes": (_i, [_vp, C.POINTER(C.c_size_t)]),
     "xlb_state_get": (_i, [_vp, _vp, C.c_size_t]),
@@ -73,6 +77,7 @@ _PROTOS = {
     "xlb_set_step_graph": (_i, [_vp, _i64]),
     "xlb_set_inlet_profile": (_i, [_vp, _vp]),
     "xlb_set_inlet_scheme": (_i, [_vp, _i]),
+    "xlb_set_inlet_normal": (_i, [_vp, _i, _i]),
     "xlb_set_wall_distances": (_i, [_vp, _i64, _vp, _vp, _vp]),
     "xlb_wall_force": (_i, [_vp, _vp]),
     "xlb_get_kernel": (_i, [_vp, C.POINTER(_i)]),
@@ -221,6 +226,51 @@ def xlb_synchronize(ctx):
     _check(load().xlb_synchronize(ctx), ctx)
 
 
+def _box(box, dims):
+    """(lo[3], hi[3]) ctypes arrays from a box given as slices in the library
+    field layout ([z, y, x] or [y, x]) or as ((lo_x, lo_y, lo_z), (hi_x, hi_y, hi_z))."""
+    if isinstance(box, tuple) and box and isinstance(box[0], slice):
+        sl = list(reversed(box)) + [slice(0, 1)] * (3 - len(box))
+        lo = [s.start or 0 for s in sl]
+        hi = [s.stop if s.stop is not None else dims[a] for a, s in enumerate(sl)]
+    else:
+        lo, hi = list(box[0]), list(box[1])
+        lo += [0] * (3 - len(lo))
+        hi += [1] * (3 - len(hi))
+    return (C.c_int64 * 3)(*[int(v) for v in lo]), (C.c_int64 * 3)(*[int(v) for v in hi])
+
+
+def xlb_kinetic_energy(ctx, box, dims, out=None):
+    """FP64 sum over the box of (1/2) rho |u|^2 of the current observables.
+    ``out``: None (returns a float), a 1-element float64 CUDA tensor (written
+    asynchronously) or a host buffer."""
+    lo, hi = _box(box, dims)
+    if out is None:
+        h = np.zeros(1, np.float64)
+        _check(load().xlb_kinetic_energy(ctx, lo, hi, h.ctypes.data), ctx)
+        return float(h[0])
+    _check(load().xlb_kinetic_energy(ctx, lo, hi, _ptr(out)), ctx)
+    return out
+
+
+def xlb_sum_squares(ctx, x, n=None, out=None):
+    """FP64 sum of squares of a float32 device buffer (returns a float, or
+    writes a 1-element float64 buffer ``out``)."""
+    if n is None:
+        n = x.size if isinstance(x, np.ndarray) else x.numel()
+    if out is None:
+        h = np.zeros(1, np.float64)
+        _check(load().xlb_sum_squares(ctx, _ptr(x), int(n), h.ctypes.data), ctx)
+        return float(h[0])
+    _check(load().xlb_sum_squares(ctx, _ptr(x), int(n), _ptr(out)), ctx)
+    return out
+
+
+def xlb_adjoint_seed_kinetic_energy(ctx, box, dims, scale=1.0):
+    lo, hi = _box(box, dims)
+    _check(load().xlb_adjoint_seed_kinetic_energy(ctx, lo, hi, float(scale)), ctx)
+
+
 def xlb_moments_noalloc(lattice, dims, storage, populations, plane_stride, mask, out, cuda_stream=None):
     """FP64 (mass, j_x, j_y, j_z) of stored populations, allocating nothing
     (the library's fixed scratch array); ``out`` holds 4 doubles (host or
@@ -310,6 +360,10 @@ def xlb_set_inlet_profile(ctx, u):
 def xlb_set_inlet_scheme(ctx, scheme):
     v = {"zou_he": XLB_INLET_ZOU_HE, "regularized": XLB_INLET_REGULARIZED}.get(scheme, scheme)
     _check(load().xlb_set_inlet_scheme(ctx, int(v)), ctx)
+
+
+def xlb_set_inlet_normal(ctx, axis, sign):
+    _check(load().xlb_set_inlet_normal(ctx, int(axis), int(sign)), ctx)
 
 
 def xlb_set_wall_distances(ctx, cells, dirs, q):
@@ -450,7 +504,8 @@ class Simulation:
         xlb_set_force(self.ctx, F)
 
     def set_kernel(self, variant="auto"):
-        v = {"auto": XLB_KERNEL_AUTO, "direct": XLB_KERNEL_DIRECT, "vec": XLB_KERNEL_VEC}.get(variant, variant)
+        v = {"auto": XLB_KERNEL_AUTO, "direct": XLB_KERNEL_DIRECT, "vec": XLB_KERNEL_VEC,
+             "vec2": XLB_KERNEL_VEC2}.get(variant, variant)
         xlb_set_kernel(self.ctx, v)
 
     def kernel(self):
@@ -464,6 +519,9 @@ class Simulation:
 
     def set_inlet_scheme(self, scheme):
         xlb_set_inlet_scheme(self.ctx, scheme)
+
+    def set_inlet_normal(self, axis, sign):
+        xlb_set_inlet_normal(self.ctx, axis, sign)
 
     def set_wall_distances(self, cells, dirs, q):
         xlb_set_wall_distances(self.ctx, cells, dirs, q)
@@ -512,6 +570,67 @@ class Simulation:
         align = 256 // raw.itemsize
         plane = (self.N + align - 1) // align * align
         return raw.reshape(self.Q, plane)[:, :self.N].reshape((self.Q,) + self.shape), kind_h
+
+
+def _autograd_function():
+    import torch
+
+    class KineticEnergyRollout(torch.autograd.Function):
+        """L(rho0[, u0]) = kinetic energy in a box after n steps from
+        f_0 = f^eq(rho0, u0), differentiable through the library's adjoint.
+
+        forward: xlb_init, xlb_tape_begin(n, k), xlb_step(n), xlb_kinetic_energy
+        (FP64, on the device).  backward: xlb_adjoint_seed_kinetic_energy
+        (scaled by the incoming cotangent), xlb_adjoint_step(n),
+        xlb_adjoint_init_grad, xlb_tape_end.  rho0 / u0 are CUDA float32
+        tensors in the library layout; the simulation's tape stays open from
+        forward to backward."""
+
+        @staticmethod
+        def forward(ctx, rho0, u0, sim, n_steps, checkpoint_every, box):
+            rho0 = rho0.detach().contiguous()
+            u0 = None if u0 is None else u0.detach().contiguous()
+            xlb_init(sim.ctx, rho0, u0)
+            xlb_tape_begin(sim.ctx, n_steps, checkpoint_every)
+            xlb_step(sim.ctx, n_steps)
+            loss = torch.empty((), dtype=torch.float64, device=rho0.device)
+            xlb_kinetic_energy(sim.ctx, box, sim.dims, loss)
+            ctx.sim, ctx.n, ctx.box = sim, n_steps, box
+            ctx.has_u0 = u0 is not None
+            ctx.shape = tuple(rho0.shape)
+            return loss
+
+        @staticmethod
+        def backward(ctx, g_out):
+            sim = ctx.sim
+            xlb_adjoint_seed_kinetic_energy(sim.ctx, ctx.box, sim.dims, float(g_out))
+            xlb_adjoint_step(sim.ctx, ctx.n)
+            g_rho = torch.empty(ctx.shape, dtype=torch.float32, device=g_out.device)
+            g_u = (torch.empty((sim.D,) + ctx.shape, dtype=torch.float32, device=g_out.device)
+                   if ctx.has_u0 else None)
+            xlb_adjoint_init_grad(sim.ctx, g_rho, g_u)
+            xlb_tape_end(sim.ctx)
+            return g_rho, g_u, None, None, None, None
+
+    return KineticEnergyRollout
+
+
+_KER = None
+
+
+def KineticEnergyRollout():
+    """The torch.autograd.Function class of the kinetic-energy rollout."""
+    global _KER
+    if _KER is None:
+        _KER = _autograd_function()
+    return _KER
+
+
+def rollout(sim, rho0, n_steps, checkpoint_every, box, u0=None):
+    """Kinetic energy in ``box`` (slices in the field layout, or ((lo), (hi))
+    in x, y, z) after ``n_steps`` of ``sim`` from f^eq(rho0, u0), as a
+    differentiable FP64 torch scalar (the gradient runs the adjoint)."""
+    return KineticEnergyRollout().apply(rho0, u0, sim, n_steps, checkpoint_every, box)
 
 
 class Batch:

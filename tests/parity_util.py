@@ -21,7 +21,7 @@ class Case:
     """One simulation set-up, runnable on the GPU and in the oracle."""
 
     def __init__(self, q, shape, omega, collision="bgk", mask=None, force=None, lid=None, inlet=None,
-                 eq=None, rho0=None, u0=None):
+                 eq=None, rho0=None, u0=None, inlet_scheme="zou_he", inlet_normal=(0, 1)):
         self.q = q
         self.lat = O.Lattice(q)
         self.shape = tuple(shape)  # (ny, nx) or (nz, ny, nx)
@@ -32,6 +32,8 @@ class Case:
         self.lid = lid      # (rho, u)
         self.inlet = inlet  # u
         self.eq = eq        # (rho, u)
+        self.inlet_scheme = inlet_scheme
+        self.inlet_normal = inlet_normal
         d = self.lat.d
         self.rho0 = rho0 if rho0 is not None else np.ones(self.shape)
         self.u0 = u0 if u0 is not None else np.zeros((d,) + self.shape)
@@ -45,7 +47,8 @@ class Case:
         bc = O.BC(d,
                   lid_u=self.lid[1][:d] if self.lid else None, lid_rho=self.lid[0] if self.lid else 1.0,
                   inlet_u=self.inlet[:d] if self.inlet else None,
-                  eq_rho=self.eq[0] if self.eq else 1.0, eq_u=self.eq[1][:d] if self.eq else None)
+                  eq_rho=self.eq[0] if self.eq else 1.0, eq_u=self.eq[1][:d] if self.eq else None,
+                  inlet_scheme=self.inlet_scheme, inlet_normal=self.inlet_normal)
         return O.Params(self.lat, self.omega, collision=self.collision,
                         force=self.force[:d] if self.force else None, bc=bc)
 
@@ -64,6 +67,10 @@ class Case:
             sim.set_bc(X.XLB_CELL_LID, self.lid[0], self.lid[1])
         if self.inlet:
             sim.set_bc(X.XLB_CELL_INLET, 1.0, self.inlet)
+        if self.inlet_scheme != "zou_he":
+            sim.set_inlet_scheme(self.inlet_scheme)
+        if tuple(self.inlet_normal) != (0, 1):
+            sim.set_inlet_normal(*self.inlet_normal)
         if self.eq:
             sim.set_bc(X.XLB_CELL_EQ, self.eq[0], self.eq[1])
         if self.force:

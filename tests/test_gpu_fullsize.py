@@ -132,7 +132,7 @@ def _crop_module():
     return mod
 
 
-@pytest.mark.parametrize("storage,tol", [("f32", 1e-4), ("f16", 5e-3), ("bf16", 5e-2)])
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-4), ("f16", 5e-3), ("bf16", 5e-3)])
 def test_kbc_sphere_crop_1000_steps_against_stored_oracle(storage, tol):
     """The KBC D3Q27 sphere channel scaled to 128 x 64 x 64 (radius 8), 1000
     steps, in the three storage forms, against the FP64 oracle's velocity

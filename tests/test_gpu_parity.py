@@ -4,8 +4,9 @@ Tolerances (relative L2 over the compared cells):
   stream only (collision NONE): bit-exact, every storage type;
   FP32 storage, FP32 arithmetic: u <= 1e-4 after 1000 steps (Taylor-Green),
     and the same bound on the shorter boundary / KBC / force cases;
-  FP16 storage of shifted populations: u <= 5e-3; BF16: reported, <= 5e-2
-    (its 8-bit mantissa puts it above the FP16 bound by design).
+  FP16 and BF16 storage of shifted populations: u <= 5e-3 (BF16 stores
+    with stochastic rounding; with round-to-nearest-even its 8-bit mantissa
+    gave 6e-3 to 8e-3 on these runs).
 """
 import numpy as np
 import pytest
@@ -72,7 +73,7 @@ def test_taylor_green_fp32_1000_steps():
     assert rel_l2(rho_g - 1, rho_o - 1) <= 1e-3
 
 
-@pytest.mark.parametrize("storage,tol", [("f16", 5e-3), ("bf16", 5e-2)])
+@pytest.mark.parametrize("storage,tol", [("f16", 5e-3), ("bf16", 5e-3)])
 def test_taylor_green_low_precision_storage(storage, tol):
     c = _tg_case()
     (rho_o, u_o), _ = c.oracle(1000)
@@ -126,7 +127,7 @@ def test_mixed_boundaries_and_force_d2q9():
     assert rel_l2(rho_g[fl] - 1, rho_o[fl] - 1) <= 1e-3
 
 
-@pytest.mark.parametrize("storage,tol", [("f32", 1e-4), ("f16", 5e-3), ("bf16", 5e-2)])
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-4), ("f16", 5e-3), ("bf16", 5e-3)])
 def test_kbc_sphere_channel_d3q27(storage, tol):
     """Zou-He inlet, outflow, halfway bounce-back sphere, KBC, D3Q27."""
     mask = I.sphere_channel_mask(48, 16, 16, radius=4, center=(14, 8, 8))

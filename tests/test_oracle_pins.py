@@ -540,18 +540,23 @@ def test_zou_he_inlet_momentum_identity():
     np.testing.assert_allclose(jx, r * uin[0], rtol=1e-13)
 
 
-@pytest.mark.parametrize("q", [9, 19, 27])
-def test_regularized_inlet_identities_and_projection(q):
-    """Regularized inlet (Latt et al. 2008): the node carries rho and
-    j = rho u_in exactly, and a state that already is regularized
-    (f^eq(rho, u_in) plus a second-order non-equilibrium part
-    w_i (c_i c_i - cs^2 I) : Pi / (2 cs^4), rho from the inlet formula) is
+NORMALS = {9: [(0, 1), (1, -1)], 19: [(0, 1), (2, -1)], 27: [(0, 1), (2, -1)]}
+
+
+@pytest.mark.parametrize("q,normal", [(q, n) for q in (9, 19, 27) for n in NORMALS[q]])
+def test_regularized_inlet_identities_and_projection(q, normal):
+    """Regularized velocity boundary (Latt et al. 2008), as an inflow (normal
+    +x) and as a moving top wall (normal -y / -z): the node carries rho and
+    j = rho u exactly, and a state that already is regularized
+    (f^eq(rho, u) plus a second-order non-equilibrium part
+    w_i (c_i c_i - cs^2 I) : Pi / (2 cs^4), rho from the boundary formula) is
     returned unchanged, whatever Pi: the rule is a projection."""
     lat = O.Lattice(q)
     shape = (4, 5) if q == 9 else (3, 4, 5)
     mask = np.full(shape, O.INLET, np.uint8)
     uin = (0.04, 0.01) if q == 9 else (0.04, 0.01, -0.02)
-    bc = O.BC(lat.d, inlet_u=uin, inlet_scheme="regularized")
+    axis, sign = normal
+    bc = O.BC(lat.d, inlet_u=uin, inlet_scheme="regularized", inlet_normal=normal)
     rng = np.random.default_rng(65)
     f = lat.w.reshape((q,) + (1,) * lat.d) * (1 + 0.05 * rng.standard_normal((q,) + shape))
     g = O.regularized_inlet(lat, f, mask, bc)
@@ -559,8 +564,8 @@ def test_regularized_inlet_identities_and_projection(q):
     j = O.momentum(lat, g)
     for a in range(lat.d):
         np.testing.assert_allclose(j[a], rho * uin[a], rtol=0, atol=1e-15)
-    # a regularized state: the inlet density formula must return its rho, so
-    # build it, then compare
+    # a regularized state: the boundary density formula must return its rho,
+    # so build it, then compare
     A = rng.standard_normal((lat.d, lat.d)) * 1e-3
     Pi = A + A.T
     u = np.stack([np.full(shape, v) for v in uin])
@@ -569,30 +574,58 @@ def test_regularized_inlet_identities_and_projection(q):
     reg = np.stack([feq[i] + lat.w[i] / (2 * O.CS2 ** 2) * sum(
         (lat.c[i, a] * lat.c[i, b] - (O.CS2 if a == b else 0.0)) * Pi[a, b]
         for a in range(lat.d) for b in range(lat.d)) for i in range(q)])
-    cx = lat.c[:, 0]
-    rho_in = (sum(reg[i] for i in range(q) if cx[i] == 0)
-              + 2 * sum(reg[i] for i in range(q) if cx[i] == -1)) / (1 - uin[0])
-    np.testing.assert_allclose(rho_in, r, rtol=1e-13)
+    cn = sign * lat.c[:, axis]
+    rho_b = (sum(reg[i] for i in range(q) if cn[i] == 0)
+             + 2 * sum(reg[i] for i in range(q) if cn[i] == -1)) / (1 - sign * uin[axis])
+    np.testing.assert_allclose(rho_b, r, rtol=1e-13)
     np.testing.assert_allclose(O.regularized_inlet(lat, reg, mask, bc), reg, rtol=0, atol=1e-15)
 
 
 @pytest.mark.parametrize("scheme", ["zou_he", "regularized"])
-def test_inlet_ignores_the_unknown_populations(scheme):
-    """Both inflow rules rebuild the populations entering the domain (c_x =
-    +1) from the known ones only: replacing the incoming unknowns by other
-    values leaves the result unchanged."""
+@pytest.mark.parametrize("normal", [(0, 1), (2, -1), (1, 1)])
+def test_inlet_ignores_the_unknown_populations(scheme, normal):
+    """Both velocity-boundary rules rebuild the populations entering the
+    fluid through the boundary (c . n = +1) from the known ones only:
+    replacing the incoming unknowns by other values leaves the result
+    unchanged."""
     lat = O.Lattice(19)
     shape = (3, 4, 5)
     mask = np.full(shape, O.INLET, np.uint8)
-    bc = O.BC(3, inlet_u=(0.05, 0.0, 0.01), inlet_scheme=scheme)
+    bc = O.BC(3, inlet_u=(0.05, 0.0, 0.01), inlet_scheme=scheme, inlet_normal=normal)
     rule = O.regularized_inlet if scheme == "regularized" else O.zou_he_inlet
     rng = np.random.default_rng(66)
     f = lat.w[:, None, None, None] * (1 + 0.05 * rng.standard_normal((19,) + shape))
     g = f.copy()
+    axis, sign = normal
     for i in range(19):
-        if lat.c[i, 0] == 1:
+        if sign * lat.c[i, axis] == 1:
             g[i] = rng.uniform(-1, 1, shape)
     np.testing.assert_allclose(rule(lat, f, mask, bc), rule(lat, g, mask, bc), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("omega,steps,tol", [(1.0, 3000, 1e-13), (1.6, 9000, 1e-11)])
+def test_regularized_moving_wall_couette_exact(omega, steps, tol):
+    """A regularized moving wall (Section 4.2's lid rule: a velocity boundary
+    with the wall's velocity parallel to it) over a halfway bounce-back floor:
+    BGK relaxes to the exact linear Couette profile, zero at the floor's wall
+    half a cell above the WALL row and U at the lid nodes,
+    u_x(y) = U (y - 1/2) / (ny - 3/2), with no density gradient."""
+    lat = O.Lattice(9)
+    H, U = 8, 0.02
+    ny = H + 2
+    mask = np.zeros((ny, 4), np.uint8)
+    mask[0, :] = O.WALL
+    mask[ny - 1, :] = O.INLET
+    bc = O.BC(2, inlet_u=(U, 0.0), inlet_scheme="regularized", inlet_normal=(1, -1))
+    p = O.Params(lat, omega, bc=bc)
+    f = O.init_state(lat, np.ones(mask.shape), np.zeros((2,) + mask.shape), mask, p)
+    f = O.run(lat, f, mask, p, steps)
+    r, u = O.macroscopic(lat, f, mask, p)
+    y = np.arange(1, ny)
+    ref = U * (y - 0.5) / (ny - 1.5)
+    np.testing.assert_allclose(u[0][1:, :], np.repeat(ref[:, None], 4, axis=1), rtol=0, atol=tol)
+    np.testing.assert_allclose(u[1][1:, :], 0.0, rtol=0, atol=tol)
+    assert np.ptp(r[1:, :]) <= 1e-12
 
 
 def _random_state(lat, shape, seed, amp=0.02):
