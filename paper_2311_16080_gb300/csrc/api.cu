@@ -47,6 +47,11 @@ struct xlb_ctx {
   long long n_links = 0;
   int* fix = nullptr;  // inlet / outlet cells (recomputed after a bulk pass)
   long long n_fix = 0;
+  void* fix_side = nullptr;  // Q x n_fix values of the storage type: their recomputed update
+  // auxiliary stream on which the fix-up cells are recomputed beside the bulk
+  // pass, with the events that fork it from and join it to the ctx stream
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int face[6] = {0, 0, 0, 0, 0, 0};  // described boundary faces (StepParams::face)
   float* link_q = nullptr;  // Bouzidi wall distance per link (LINK_BZ entries), or null
   float* inlet_field = nullptr;  // D * N inlet velocities (xlb_set_inlet_profile), or null
@@ -271,11 +276,12 @@ static bool use_vec(const xlb_ctx* c) {
 
 // Boundary pass on dst after a pass that produced post-collision values
 // there: ghost values of every link and of the inlet / outlet cells' links;
-// with `fix_src`, the inlet / outlet cells are first recomputed from it.
+// with `fix_src`, the inlet / outlet cells are first recomputed from it (or,
+// with `from_side`, their recomputation is taken from the side buffer).
 // Without it (the state came from a local collision or a restore, not from
 // the bulk kernel, which pushes them itself), the ghost values of the
 // boundary faces are written first.
-static int boundary_pass(xlb_ctx* c, const void* fix_src, void* dst) {
+static int boundary_pass(xlb_ctx* c, const void* fix_src, void* dst, bool from_side = false) {
   if (!c->has_mask) return XLB_OK;
   if (!fix_src) {
     bool faces = false;
@@ -296,7 +302,8 @@ static int boundary_pass(xlb_ctx* c, const void* fix_src, void* dst) {
   a.n_links = c->n_links;
   a.fix = c->fix;
   a.n_fix = c->n_fix;
-  a.recompute = fix_src ? 1 : 0;
+  a.fix_mode = fix_src ? (from_side ? FIX_SIDE_COMMIT : FIX_RECOMPUTE) : FIX_STORED;
+  a.side = c->fix_side;
   return dispatch(c, OP_BOUNDARY, a);
 }
 
@@ -305,6 +312,13 @@ static int boundary_pass(xlb_ctx* c, const void* fix_src, void* dst) {
 // the wall, lid and EQ cells hold ghost values that make that pull exact --
 // then the boundary pass, which rewrites the ghosts for the next step and
 // recomputes the inlet / outlet cells.
+// The fix-up cells' recomputation reads only src, so it runs on the
+// auxiliary stream beside the bulk pass (forked from and joined back to the
+// ctx stream by events, which a graph capture turns into parallel branches)
+// and leaves its results in the side buffer; the boundary pass after the
+// bulk pass stores them and writes their ghost values.  On small lattices
+// with many inlet / outlet cells this takes their serial recomputation off
+// the critical path.
 static int launch_step(xlb_ctx* c, const void* src, void* dst) {
   const bool vec = use_vec(c);
   LaunchArgs a = base_args(c);
@@ -313,8 +327,30 @@ static int launch_step(xlb_ctx* c, const void* src, void* dst) {
   a.vec_width = c->variant == XLB_KERNEL_VEC2 ? 2 : 4;
   a.p.has_mask = 0;  // bulk pass: every cell pulled as if periodic
   cudaEvent_t* pe = prof_begin(c, 0);
-  int r = dispatch(c, vec ? OP_STEP_VEC : OP_STEP, a);
-  if (!r) r = boundary_pass(c, src, dst);
+  const bool side = c->has_mask && c->n_fix > 0 && c->fix_side && c->aux;
+  int r = XLB_OK;
+  if (side) {
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    LaunchArgs f = base_args(c);
+    f.src = src;
+    f.dst = dst;
+    f.fix = c->fix;
+    f.n_fix = c->n_fix;
+    f.fix_mode = FIX_SIDE_COMPUTE;
+    f.side = c->fix_side;
+    f.stream = c->aux;
+    r = dispatch(c, OP_BOUNDARY, f);
+    cudaError_t e = cudaEventRecord(c->ev_join, c->aux);
+    if (!r && e != cudaSuccess) r = cuda_fail(c, e, "cudaEventRecord(join)");
+  }
+  if (!r) r = dispatch(c, vec ? OP_STEP_VEC : OP_STEP, a);
+  if (side) {
+    // join even after a failure, so that a capture in progress stays whole
+    cudaError_t e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    if (!r && e != cudaSuccess) r = cuda_fail(c, e, "cudaStreamWaitEvent(join)");
+  }
+  if (!r) r = boundary_pass(c, src, dst, side);
   prof_end(c, pe);
   return r;
 }
@@ -534,6 +570,10 @@ int xlb_create(xlb_ctx** out, int lattice, const int64_t dims[3], double omega, 
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemset(error words)"));
   e = cudaMalloc(&c->init_fields, sizeof(float) * (size_t)(1 + c->D) * (size_t)c->N);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(init fields)"));
+  e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "auxiliary stream"));
   *out = c;
   return XLB_OK;
 }
@@ -556,6 +596,13 @@ void xlb_destroy(xlb_ctx* c) {
   if (c->inlet_field) cudaFree(c->inlet_field);
   if (c->fix) cudaFree(c->fix);
   if (c->init_fields) cudaFree(c->init_fields);
+  if (c->fix_side) cudaFree(c->fix_side);
+  if (c->aux) {
+    cudaStreamSynchronize(c->aux);
+    cudaStreamDestroy(c->aux);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->partial) cudaFree(c->partial);
   if (c->red_out) cudaFree(c->red_out);
   if (c->stage) cudaFree(c->stage);
@@ -674,10 +721,22 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
       return r;
     }
   }
+  void* nside = nullptr;
+  if (nfx > 0) {
+    const cudaError_t e = cudaMalloc(&nside, (size_t)c->esize * (size_t)c->Q * (size_t)nfx);
+    if (e != cudaSuccess) {
+      cudaFree(nf);
+      if (nlinks) cudaFree(nlinks);
+      if (nfix) cudaFree(nfix);
+      return cuda_fail(c, e, "cudaMalloc(fix-up side buffer)");
+    }
+  }
   if (c->flags) cudaFree(c->flags);
   if (c->links) cudaFree(c->links);
   if (c->link_q) cudaFree(c->link_q);
   c->link_q = nullptr;  // wall distances belong to the old link table
+  if (c->fix_side) cudaFree(c->fix_side);
+  c->fix_side = nside;
   if (c->fix) cudaFree(c->fix);
   c->flags = nf;
   c->links = nlinks;

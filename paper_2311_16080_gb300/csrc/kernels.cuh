@@ -338,17 +338,25 @@ __device__ __forceinline__ float bouzidi_ghost(const S* __restrict__ dst, const 
 // Threads [0, ceil(n_links / 4)) write the ghost values of the links of FLUID
 // cells and of cells on FWALL face planes (4 links each; LINK_BZ links take
 // the Bouzidi value with link_q[e]); the next n_fix threads handle one INLET,
-// OUTLET or other FWALL cell each: with `recompute`, its update from src with
-// the full rules (the bulk pass pulled and collided it as if periodic fluid);
-// then the ghosts of its own links.  src is read only by the recomputation,
-// which needs the ghosts of the previous state, already in src.
+// OUTLET or other FWALL cell each (the bulk pass pulled and collided it as if
+// periodic fluid), by `mode` (FixMode):
+//   FIX_RECOMPUTE:    its update from src with the full rules, stored in dst;
+//   FIX_SIDE_COMPUTE: the same update stored in the side buffer
+//                     side[i * n_fix + k] only (this mode runs beside the
+//                     bulk pass, which it does not depend on);
+//   FIX_SIDE_COMMIT:  the values of the side buffer stored in dst;
+//   FIX_STORED:       the values already in dst;
+// then (all but FIX_SIDE_COMPUTE) the ghosts of its own links.  src is read
+// only by the recomputation, which needs the ghosts of the previous state,
+// already in src.
 constexpr int LINKS_PER_THREAD = 4;
 
 template <int Q, typename S, int COLL>
 __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ src, S* __restrict__ dst,
                                                         const StepParams p, const int2* __restrict__ links,
                                                         const float* __restrict__ link_q, int n_links,
-                                                        const int* __restrict__ fix, int n_fix, int recompute) {
+                                                        const int* __restrict__ fix, int n_fix, int mode,
+                                                        S* __restrict__ side) {
   // link threads: LINKS_PER_THREAD links each, strided by the link-thread
   // count so that a warp's loads and stores stay on consecutive entries
   const int n_lt = (n_links + LINKS_PER_THREAD - 1) / LINKS_PER_THREAD;
@@ -394,7 +402,7 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ sr
   Nbr nb;
   make_nbr(nb, x, y, z, p.nx, p.ny, p.nz);
   float df[Q];
-  if (recompute) {
+  if (mode == FIX_RECOMPUTE || mode == FIX_SIDE_COMPUTE) {
     const int type = __ldg(p.flags + self) & FLAG_TYPE;
     pull_cell<Q, S>(src, p, x, y, z, type, nb, df);
     if (type == FWALL) {
@@ -404,11 +412,25 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ sr
     }
     CellRound<S> rnd;
     rnd.begin((uint32_t)self, df);
+    if (mode == FIX_SIDE_COMPUTE) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) rnd.st(side + (long long)i * n_fix + kf, i, df[i]);
+      return;
+    }
     S* out = dst + self;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       rnd.st(out, i, df[i]);
       df[i] = rnd.rounded(i, df[i]);  // the stored value, as the link threads read it
+      out += p.plane;
+    }
+  } else if (mode == FIX_SIDE_COMMIT) {
+    S* out = dst + self;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const S v = side[(long long)i * n_fix + kf];
+      *out = v;
+      df[i] = Store<S>::ld_plain(&v);
       out += p.plane;
     }
   } else {
@@ -855,7 +877,8 @@ int launch_typed(Op op, const LaunchArgs& a) {
       if (tot > 0x7fffffffLL) return -1;
       const unsigned g = (unsigned)((tot + ROW_BLOCK - 1) / ROW_BLOCK);
       k_boundary<Q, S, COLL><<<g, ROW_BLOCK, 0, st>>>((const S*)a.src, (S*)a.dst, p, a.links, a.link_q,
-                                                     (int)a.n_links, a.fix, (int)a.n_fix, a.recompute);
+                                                     (int)a.n_links, a.fix, (int)a.n_fix, a.fix_mode,
+                                                     (S*)a.side);
       return 0;
     }
     case OP_COLLIDE_LOCAL:

@@ -42,11 +42,15 @@ struct LaunchArgs {
   long long n_links;
   const int* fix;              // OP_BOUNDARY fix-up cells (INLET, OUTLET, FWALL off the faces)
   long long n_fix;
-  int recompute;               // OP_BOUNDARY: recompute the fix-up cells from src
+  int fix_mode;                // OP_BOUNDARY: how the fix-up cells are handled (FixMode)
+  void* side;                  // OP_BOUNDARY: Q x n_fix side buffer of the storage type
   int box_lo[3], box_ext[3];   // OP_KE_PARTIAL: first cell and extent of the box per axis
   int vec_width;               // OP_STEP_VEC: cells per thread (2 or 4)
   void* stream;
 };
+
+// Fix-up cells in the boundary pass (k_boundary).
+enum FixMode { FIX_STORED = 0, FIX_RECOMPUTE = 1, FIX_SIDE_COMMIT = 2, FIX_SIDE_COMPUTE = 3 };
 
 // Returns 0 on a successful launch request, a negative code for an invalid
 // combination (the caller then reports XLB_ERR_ARG / XLB_ERR_UNSUPPORTED).
