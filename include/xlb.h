@@ -124,7 +124,8 @@ int xlb_set_mask(xlb_ctx* ctx, const uint8_t* mask);
 
 /* Sizes of the boundary tables of the current mask.  Whole face planes that
  * the mask fills with one boundary type are handled by coordinates and need
- * no table.  n_links = number of (cell, direction) pairs, over FLUID cells
+ * no table (with 16-bit storage the WALL / LID / EQ planes x = 0 and
+ * x = nx - 1 are served by the table instead).  n_links = number of (cell, direction) pairs, over FLUID cells
  * and FWALL cells of FWALL face planes, whose source cell is WALL, LID or EQ
  * off the face planes; n_fix = number of INLET and OUTLET cells plus the
  * FWALL cells off the face planes.  After each update a boundary pass
@@ -356,17 +357,17 @@ int xlb_tape_release(xlb_ctx* ctx);
  *     per direction, the +-x neighbour element exchanged by warp shuffles
  *     (16-bit storage, D2Q9 / D3Q19, BGK, nx % 4 == 0);
  *   XLB_KERNEL_VEC2:   the same with 2 cells per thread and 32-bit words
- *     (nx even; chosen only on request);
- *   XLB_KERNEL_AUTO:   VEC where possible on lattices without boundary faces
- *     (whole face planes the mask fills with one boundary type), else DIRECT
- *     (the default).
+ *     (nx even);
+ *   XLB_KERNEL_AUTO:   the default: with FP16 storage VEC on lattices without
+ *     boundary planes and VEC2 with them, else DIRECT (the fastest measured
+ *     on 256^3 D3Q19 lattices; BF16 and FP32 run DIRECT).
  * A mask with an FWALL face plane always runs DIRECT. */
 enum { XLB_KERNEL_AUTO = 0, XLB_KERNEL_DIRECT = 1, XLB_KERNEL_VEC = 2, XLB_KERNEL_VEC2 = 3 };
 
 /* Choose the variant (XLB_ERR_UNSUPPORTED if it cannot run this ctx). */
 int xlb_set_kernel(xlb_ctx* ctx, int variant);
 
-/* The variant the next update launches (DIRECT or VEC). */
+/* The variant the next update launches (DIRECT, VEC or VEC2). */
 int xlb_get_kernel(const xlb_ctx* ctx, int* variant);
 
 /* ---- batched small 2D domains (Section 6 batching) --------------------- */

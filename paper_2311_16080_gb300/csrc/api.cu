@@ -53,6 +53,7 @@ struct xlb_ctx {
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int face[6] = {0, 0, 0, 0, 0, 0};  // described boundary faces (StepParams::face)
+  bool x_linked = false;             // the x-faces' sources are served by ghost links
   float* link_q = nullptr;  // Bouzidi wall distance per link (LINK_BZ entries), or null
   float* inlet_field = nullptr;  // D * N inlet velocities (xlb_set_inlet_profile), or null
   int inlet_scheme = XLB_INLET_ZOU_HE;
@@ -183,6 +184,7 @@ static StepParams make_params(const xlb_ctx* c) {
     p.face[f] = c->face[f];
     p.has_faces |= c->face[f] != 0;
   }
+  p.x_linked = c->x_linked ? 1 : 0;
   // constant boundary terms per direction, in double then rounded once
   auto fill = [&](auto lat_tag) {
     constexpr int Q = decltype(lat_tag)::value;
@@ -262,17 +264,27 @@ static bool has_fwall_face(const xlb_ctx* c) {
   return false;
 }
 
-// AUTO takes VEC only on lattices without boundary faces: with faces, every
-// warp of a 4-cell-per-thread row holds a face-adjacent lane (measured slower
-// than one cell per thread on the 256^3 cavity).
-static bool use_vec(const xlb_ctx* c) {
-  if (c->variant == XLB_KERNEL_VEC2) return vec_possible(c, 2) && !has_fwall_face(c);
-  if (c->variant == XLB_KERNEL_DIRECT || !vec_possible(c) || has_fwall_face(c)) return false;
-  if (c->variant == XLB_KERNEL_VEC) return true;
-  for (int f = 0; f < 6; ++f)
-    if (c->face[f]) return false;
-  return true;
+// The bulk variant an update launches: the requested one where it can run
+// this ctx, and for AUTO the fastest measured on the 256^3 D3Q19 lattices
+// (periodic box and cavity): with FP16 storage 4 cells per thread without
+// boundary faces (70.4 k MLUPS against 66.3 k for one cell per thread) and 2
+// cells per thread with them (59.0 k against 57.3 k); with BF16 storage
+// (whose stochastic rounding adds per-value work) and FP32 one cell per
+// thread.  Masks with FWALL faces always run one cell per thread.
+static int bulk_variant(const xlb_ctx* c) {
+  if (c->variant == XLB_KERNEL_DIRECT || has_fwall_face(c)) return XLB_KERNEL_DIRECT;
+  if (c->variant == XLB_KERNEL_VEC2) return vec_possible(c, 2) ? XLB_KERNEL_VEC2 : XLB_KERNEL_DIRECT;
+  if (c->variant == XLB_KERNEL_VEC) return vec_possible(c, 4) ? XLB_KERNEL_VEC : XLB_KERNEL_DIRECT;
+  if (c->storage != XLB_STORE_F16) return XLB_KERNEL_DIRECT;
+  bool faces = false;
+  for (int f = 0; f < 6; ++f) faces |= c->face[f] != 0;
+  if (c->has_mask && c->n_links > 0) faces = true;  // boundary planes served by ghost links
+  if (!faces && vec_possible(c, 4)) return XLB_KERNEL_VEC;
+  if (vec_possible(c, 2)) return XLB_KERNEL_VEC2;
+  return XLB_KERNEL_DIRECT;
 }
+
+static bool use_vec(const xlb_ctx* c) { return bulk_variant(c) != XLB_KERNEL_DIRECT; }
 
 // Boundary pass on dst after a pass that produced post-collision values
 // there: ghost values of every link and of the inlet / outlet cells' links;
@@ -324,7 +336,7 @@ static int launch_step(xlb_ctx* c, const void* src, void* dst) {
   LaunchArgs a = base_args(c);
   a.src = src;
   a.dst = dst;
-  a.vec_width = c->variant == XLB_KERNEL_VEC2 ? 2 : 4;
+  a.vec_width = bulk_variant(c) == XLB_KERNEL_VEC2 ? 2 : 4;
   a.p.has_mask = 0;  // bulk pass: every cell pulled as if periodic
   cudaEvent_t* pe = prof_begin(c, 0);
   const bool side = c->has_mask && c->n_fix > 0 && c->fix_side && c->aux;
@@ -660,6 +672,17 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
     new_io = io;
     detect_faces(hp, c->nx, c->ny, c->nz, new_face);
   }
+  // With 16-bit storage the bulk pass is bound by instruction issue, and the
+  // x-face rules would run in diverging lanes at both ends of every row: the
+  // sources on WALL / LID / EQ x-face planes (outside the skipped y / z face
+  // rows) go to the ghost links instead, written by the boundary pass after
+  // each update.  The x-faces still take part in deriving the rule of the
+  // cells where planes meet.  Lattices with an FWALL x-face keep the rules in
+  // the pull.
+  const bool new_x_linked = c->esize == 2 && (new_face[0] || new_face[1]) && new_face[0] != XLB_CELL_FWALL &&
+                            new_face[1] != XLB_CELL_FWALL;
+  int link_face[6];
+  for (int f = 0; f < 6; ++f) link_face[f] = (new_x_linked && f < 2) ? 0 : new_face[f];
   // boundary tables: ghost links (direction-major) and inlet / outlet cells
   int2* nlinks = nullptr;
   int* nfix = nullptr;
@@ -675,7 +698,7 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
     // passes 1..Q-1: links of direction i; pass Q: inlet / outlet cells
     for (int pass = 1; pass <= c->Q && e == cudaSuccess; ++pass) {
       const int mode = pass == c->Q ? 1 : 0;
-      if (launch_pred_count(mode, pass, c->Q, new_face, nf, (int)c->nx, (int)c->ny, (int)c->nz, counts + nb * pass,
+      if (launch_pred_count(mode, pass, c->Q, link_face, nf, (int)c->nx, (int)c->ny, (int)c->nz, counts + nb * pass,
                             c->stream) != 0)
         e = cudaErrorInvalidValue;
     }
@@ -698,7 +721,7 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
     for (int pass = 1; pass <= c->Q && e == cudaSuccess; ++pass) {
       const int mode = pass == c->Q ? 1 : 0;
       if ((mode == 0 && nl == 0) || (mode == 1 && nfx == 0)) continue;
-      if (launch_pred_write(mode, pass, c->Q, new_face, nf, (int)c->nx, (int)c->ny, (int)c->nz, offs + nb * pass,
+      if (launch_pred_write(mode, pass, c->Q, link_face, nf, (int)c->nx, (int)c->ny, (int)c->nz, offs + nb * pass,
                             nlinks, nfix, c->stream) != 0)
         e = cudaErrorInvalidValue;
     }
@@ -745,6 +768,7 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
   c->n_fix = nfx;
   c->has_inlet_outlet = new_io;
   for (int f = 0; f < 6; ++f) c->face[f] = new_face[f];
+  c->x_linked = new_x_linked;
   c->has_mask = true;
   ++c->epoch;
   return XLB_OK;
@@ -1080,7 +1104,7 @@ int xlb_set_kernel(xlb_ctx* c, int variant) {
 
 int xlb_get_kernel(const xlb_ctx* c, int* variant) {
   if (!c || !variant) return XLB_ERR_ARG;
-  *variant = use_vec(c) ? (c->variant == XLB_KERNEL_VEC2 ? XLB_KERNEL_VEC2 : XLB_KERNEL_VEC) : XLB_KERNEL_DIRECT;
+  *variant = bulk_variant(c);
   return XLB_OK;
 }
 

@@ -87,9 +87,18 @@ __device__ __forceinline__ int fc_type(uint32_t fc, int axis, int k) { return (i
 template <bool FW>
 __device__ __forceinline__ uint32_t face_code(const StepParams& p, int x, int y, int z) {
   if (!p.has_faces) return 0u;
-  // a cell two or more planes away from every boundary plane has no face
-  // coordinate among its own and its neighbours'
-  if (x > 1 && x < p.nx - 2 && y > 1 && y < p.ny - 2 && (p.nz == 1 || (z > 1 && z < p.nz - 2))) return 0u;
+  // a row two or more planes away from the y / z boundary planes (uniform
+  // over a warp, which covers one row) can only meet x-faces: their types
+  // follow from four compares per lane
+  if (y > 1 && y < p.ny - 2 && (p.nz == 1 || (z > 1 && z < p.nz - 2))) {
+    const int tm = (x == 1 ? p.face[0] : 0) | (x == 0 ? p.face[1] : 0);           // x - 1
+    const int ts = (x == 0 ? p.face[0] : 0) | (x == p.nx - 1 ? p.face[1] : 0);    // x
+    const int tp = (x == p.nx - 1 ? p.face[0] : 0) | (x == p.nx - 2 ? p.face[1] : 0);  // x + 1
+    uint32_t fc = (uint32_t)tm | (uint32_t)ts << 3 | (uint32_t)tp << 6;
+    if (!p.x_linked && (tm | tp) != 0 && (ts == 0 || (FW && ts == FWALL))) fc |= FC_XN;
+    if (FW && ts == FWALL) fc |= FC_FWALL;
+    return fc;
+  }
   int tx[3], ty[3], tz[3];
   axis_face_types(x, p.nx, p.face[0], p.face[1], tx);
   axis_face_types(y, p.ny, p.face[2], p.face[3], ty);
@@ -100,7 +109,7 @@ __device__ __forceinline__ uint32_t face_code(const StepParams& p, int x, int y,
     fc |= (uint32_t)tx[k] << (3 * k) | (uint32_t)ty[k] << (3 * (3 + k)) | (uint32_t)tz[k] << (3 * (6 + k));
   // x-face sources matter to cells that hold state: not to the boundary
   // cells of an x-face plane themselves (FWALL ones do hold state)
-  if ((tx[0] | tx[2]) != 0 && (tx[1] == 0 || (FW && tx[1] == FWALL))) fc |= FC_XN;
+  if (!p.x_linked && (tx[0] | tx[2]) != 0 && (tx[1] == 0 || (FW && tx[1] == FWALL))) fc |= FC_XN;
   if ((ty[0] | ty[1] | ty[2] | tz[0] | tz[1] | tz[2]) != 0) fc |= FC_RN;
   const int self = face_combine<FW>(tx[1], ty[1], tz[1]);
   if (self != 0 && face_combine<FW>(0, ty[1], tz[1]) != 0)
@@ -519,8 +528,9 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
     base += p.plane;
   }
   const int self0 = x0 + nx * row;
-  // sources on x-face planes (only the lanes at the ends of a row have them)
-  if (p.has_faces && (x0 <= 1 || x0 + V >= nx - 1)) {
+  // sources on x-face planes (only the lanes at the ends of a row have them;
+  // none when ghost links serve them)
+  if (p.has_faces && !p.x_linked && (x0 <= 1 || x0 + V >= nx - 1)) {
 #pragma unroll
     for (int k = 0; k < V; ++k) {
       int tx[3];

@@ -55,6 +55,9 @@ struct StepParams {
   // colliding; every other WALL / LID / EQ source uses ghost values.
   int face[6];
   int has_faces;
+  // 16-bit bulk passes: the sources on the x-face planes outside the skipped
+  // y / z face rows are served by ghost links, not by rules in the pull
+  int x_linked;
   // bulk kernels: 1 when launched on a (x-blocks, ny, nz) grid, 0 when the
   // grid is flattened over rows (ny or nz above the grid limit)
   int grid3;

@@ -96,21 +96,39 @@ def test_vec_f16_matches_oracle(name, case):
     assert rel_l2(u_g[:, fl], u_o[:, fl]) <= 5e-3
 
 
-def test_auto_picks_vec_for_16_bit_storage_only():
+def test_auto_picks_the_variant_by_storage():
+    """AUTO: FP16 runs 4 cells per thread without boundary planes and 2 with
+    them; BF16 and FP32 one cell per thread; VEC needs 16-bit storage."""
     m = I.lid_driven_cavity_mask(32, 8, 8)
     c = Case(19, m.shape, 1.5, "bgk", mask=m)
     s32 = c.gpu_sim("f32")
     s16 = c.gpu_sim("f16")
+    sb16 = c.gpu_sim("bf16")
     assert s32.kernel() == X.XLB_KERNEL_DIRECT
-    assert s16.kernel() == X.XLB_KERNEL_DIRECT  # the cavity's walls are faces
+    assert s16.kernel() == X.XLB_KERNEL_VEC2  # the cavity's walls
+    assert sb16.kernel() == X.XLB_KERNEL_DIRECT
     per16 = Case(19, (8, 8, 32), 1.5, "bgk").gpu_sim("f16")
     assert per16.kernel() == X.XLB_KERNEL_VEC
     with pytest.raises(X.XlbError) as e:
         X.xlb_set_kernel(s32.ctx, X.XLB_KERNEL_VEC)
     assert e.value.status == X.XLB_ERR_UNSUPPORTED
     odd = Case(9, (30, 45), 1.2).gpu_sim("f16")
-    assert odd.kernel() == X.XLB_KERNEL_DIRECT  # nx % 4 != 0
-    for s in (s32, s16, odd, per16):
+    assert odd.kernel() == X.XLB_KERNEL_DIRECT  # nx odd
+    for s in (s32, s16, sb16, odd, per16):
+        s.close()
+
+
+def test_16_bit_x_faces_are_served_by_ghost_links():
+    """With 16-bit storage the WALL / LID / EQ x-face planes are boundary
+    links (the bulk pass then runs no face logic at the ends of a row); the
+    y / z faces stay faces.  FP32 keeps all six faces."""
+    m = I.lid_driven_cavity_mask(20, 18, 16)
+    want16 = _links(19, m, [(1, 0), (1, -1), (0, 0), (0, -1)])
+    assert want16 > 0
+    for st, want in (("f32", 0), ("f16", want16), ("bf16", want16)):
+        s = X.Simulation(19, (20, 18, 16), 1.5, "bgk", st)
+        s.set_mask(m)
+        assert X.xlb_boundary_links(s.ctx) == (want, 0)
         s.close()
 
 
