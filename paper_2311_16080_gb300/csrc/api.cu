@@ -45,6 +45,7 @@ struct xlb_ctx {
   bool has_mask = false;
   int2* links = nullptr;  // ghost links {cell, dir | type << 8} of the mask
   long long n_links = 0;
+  int2* link_cells = nullptr;        // per link: source cell, Bouzidi partner (k_link_cells)
   int* fix = nullptr;  // inlet / outlet cells (recomputed after a bulk pass)
   long long n_fix = 0;
   void* fix_side = nullptr;  // Q x n_fix values of the storage type: their recomputed update
@@ -54,6 +55,7 @@ struct xlb_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int face[6] = {0, 0, 0, 0, 0, 0};  // described boundary faces (StepParams::face)
   bool x_linked = false;             // the x-faces' sources are served by ghost links
+  bool x_inrow = false;              // ... or by in-row ghost values of the face cells
   float* link_q = nullptr;  // Bouzidi wall distance per link (LINK_BZ entries), or null
   float* inlet_field = nullptr;  // D * N inlet velocities (xlb_set_inlet_profile), or null
   int inlet_scheme = XLB_INLET_ZOU_HE;
@@ -185,6 +187,7 @@ static StepParams make_params(const xlb_ctx* c) {
     p.has_faces |= c->face[f] != 0;
   }
   p.x_linked = c->x_linked ? 1 : 0;
+  p.x_inrow = c->x_inrow ? 1 : 0;
   // constant boundary terms per direction, in double then rounded once
   auto fill = [&](auto lat_tag) {
     constexpr int Q = decltype(lat_tag)::value;
@@ -310,6 +313,7 @@ static int boundary_pass(xlb_ctx* c, const void* fix_src, void* dst, bool from_s
   a.src = fix_src ? fix_src : dst;
   a.dst = dst;
   a.links = c->links;
+  a.link_cells = c->link_cells;
   a.link_q = c->link_q;
   a.n_links = c->n_links;
   a.fix = c->fix;
@@ -604,6 +608,7 @@ void xlb_destroy(xlb_ctx* c) {
     if (c->buf[k]) cudaFree(c->buf[k]);
   if (c->flags) cudaFree(c->flags);
   if (c->links) cudaFree(c->links);
+  if (c->link_cells) cudaFree(c->link_cells);
   if (c->link_q) cudaFree(c->link_q);
   if (c->inlet_field) cudaFree(c->inlet_field);
   if (c->fix) cudaFree(c->fix);
@@ -646,18 +651,21 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
   int new_face[6] = {0, 0, 0, 0, 0, 0};
   CK(cudaMalloc(&nf, n));
   CK(cudaMemsetAsync(c->err_word, 0, sizeof(int), c->stream));
+  CK(cudaMemsetAsync(c->err_word + 2, 0, sizeof(int), c->stream));
   if (launch_mask_prepare(c->Q, dmask, nf, (int)c->nx, (int)c->ny, (int)c->nz, c->err_word, c->stream) != 0) {
     cudaFree(nf);
     return fail(c, XLB_ERR_ARG, "mask preparation rejected");
   }
-  int herr = 0;
-  CK(cudaMemcpyAsync(&herr, c->err_word, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  int hw[3] = {0, 0, 0};  // bad code; the device error word (not used here); inlet / outlet / FWALL seen
+  CK(cudaMemcpyAsync(hw, c->err_word, sizeof(hw), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  const int herr = hw[0];
   if (herr) {
     cudaFree(nf);
     return fail(c, XLB_ERR_ARG, "mask holds a code >= 7");
   }
-  // does the mask hold inlet / outlet / FWALL cells (adjoint support check)?
+  // inlet / outlet / FWALL cells anywhere (the adjoint support check), from
+  // the preparation kernel; the boundary faces, from the mask's face planes
   {
     std::vector<uint8_t> h;
     const uint8_t* hp = mask;
@@ -666,25 +674,30 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
       CK(cudaMemcpy(h.data(), mask, n, cudaMemcpyDeviceToHost));
       hp = h.data();
     }
-    bool io = false;
-    for (size_t k = 0; k < n && !io; ++k)
-      io = (hp[k] == XLB_CELL_INLET || hp[k] == XLB_CELL_OUTLET || hp[k] == XLB_CELL_FWALL);
-    new_io = io;
+    new_io = hw[2] != 0;
     detect_faces(hp, c->nx, c->ny, c->nz, new_face);
   }
   // With 16-bit storage the bulk pass is bound by instruction issue, and the
-  // x-face rules would run in diverging lanes at both ends of every row: the
-  // sources on WALL / LID / EQ x-face planes (outside the skipped y / z face
-  // rows) go to the ghost links instead, written by the boundary pass after
-  // each update.  The x-faces still take part in deriving the rule of the
-  // cells where planes meet.  Lattices with an FWALL x-face keep the rules in
-  // the pull.
-  const bool new_x_linked = c->esize == 2 && (new_face[0] || new_face[1]) && new_face[0] != XLB_CELL_FWALL &&
-                            new_face[1] != XLB_CELL_FWALL;
+  // x-face rules would run in diverging lanes at both ends of every row.
+  // With WALL / LID / EQ faces at both x = 0 and x = nx - 1 and no FWALL face
+  // the face cell of each row holds, in the directions crossing the face, the
+  // rule's value for its neighbour in the row, stored with the row by the bulk
+  // pass (in-row ghosts; the neighbour's lane and the face cell's lane must
+  // share a warp, so nx = 1 mod 32 is left out).  Otherwise the sources on
+  // WALL / LID / EQ x-face planes (outside the skipped y / z face rows) go to
+  // the ghost links, written by the boundary pass after each update.  The
+  // x-faces still take part in deriving the rule of the cells where planes
+  // meet.  Lattices with an FWALL x-face keep the rules in the pull.
+  bool any_fwall_face = false;
+  for (int f = 0; f < 6; ++f) any_fwall_face |= new_face[f] == XLB_CELL_FWALL;
+  const bool new_x_inrow = c->esize == 2 && new_face[0] && new_face[1] && !any_fwall_face && c->nx % 32 != 1;
+  const bool new_x_linked = c->esize == 2 && !new_x_inrow && (new_face[0] || new_face[1]) &&
+                            new_face[0] != XLB_CELL_FWALL && new_face[1] != XLB_CELL_FWALL;
   int link_face[6];
   for (int f = 0; f < 6; ++f) link_face[f] = (new_x_linked && f < 2) ? 0 : new_face[f];
   // boundary tables: ghost links (direction-major) and inlet / outlet cells
   int2* nlinks = nullptr;
+  int2* nlcells = nullptr;
   int* nfix = nullptr;
   long long nl = 0, nfx = 0;
   {
@@ -717,6 +730,7 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
                           c->stream);
     }
     if (e == cudaSuccess && nl > 0) e = cudaMalloc(&nlinks, sizeof(int2) * nl);
+    if (e == cudaSuccess && nl > 0) e = cudaMalloc(&nlcells, sizeof(int2) * nl);
     if (e == cudaSuccess && nfx > 0) e = cudaMalloc(&nfix, sizeof(int) * nfx);
     for (int pass = 1; pass <= c->Q && e == cudaSuccess; ++pass) {
       const int mode = pass == c->Q ? 1 : 0;
@@ -725,12 +739,16 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
                             nlinks, nfix, c->stream) != 0)
         e = cudaErrorInvalidValue;
     }
+    if (e == cudaSuccess && nl > 0 &&
+        launch_link_cells(c->Q, nlinks, nl, nf, (int)c->nx, (int)c->ny, (int)c->nz, nlcells, c->stream) != 0)
+      e = cudaErrorInvalidValue;
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (counts) cudaFree(counts);
     if (offs) cudaFree(offs);
     if (e != cudaSuccess) {
       cudaFree(nf);
       if (nlinks) cudaFree(nlinks);
+      if (nlcells) cudaFree(nlcells);
       if (nfix) cudaFree(nfix);
       return cuda_fail(c, e, "boundary tables");
     }
@@ -740,6 +758,7 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
     if (r) {
       cudaFree(nf);
       if (nlinks) cudaFree(nlinks);
+      if (nlcells) cudaFree(nlcells);
       if (nfix) cudaFree(nfix);
       return r;
     }
@@ -750,12 +769,14 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
     if (e != cudaSuccess) {
       cudaFree(nf);
       if (nlinks) cudaFree(nlinks);
+      if (nlcells) cudaFree(nlcells);
       if (nfix) cudaFree(nfix);
       return cuda_fail(c, e, "cudaMalloc(fix-up side buffer)");
     }
   }
   if (c->flags) cudaFree(c->flags);
   if (c->links) cudaFree(c->links);
+  if (c->link_cells) cudaFree(c->link_cells);
   if (c->link_q) cudaFree(c->link_q);
   c->link_q = nullptr;  // wall distances belong to the old link table
   if (c->fix_side) cudaFree(c->fix_side);
@@ -763,12 +784,14 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
   if (c->fix) cudaFree(c->fix);
   c->flags = nf;
   c->links = nlinks;
+  c->link_cells = nlcells;
   c->n_links = nl;
   c->fix = nfix;
   c->n_fix = nfx;
   c->has_inlet_outlet = new_io;
   for (int f = 0; f < 6; ++f) c->face[f] = new_face[f];
   c->x_linked = new_x_linked;
+  c->x_inrow = new_x_inrow;
   c->has_mask = true;
   ++c->epoch;
   return XLB_OK;

@@ -50,10 +50,13 @@ __device__ __forceinline__ bool cell_of_grid(const StepParams& p, CellIdx& c) {
 #ifndef XLB_MINB_Q19_16
 #define XLB_MINB_Q19_16 9
 #endif
+#ifndef XLB_MINB_KBC
+#define XLB_MINB_KBC 6
+#endif
 template <int Q, typename S, int COLL>
 struct MinBlocks {
   static constexpr int value =
-      (COLL == 2) ? 5 : (Q == 27 ? 8 : (Q == 19 ? (sizeof(S) == 2 ? XLB_MINB_Q19_16 : 9) : 12));
+      (COLL == 2) ? XLB_MINB_KBC : (Q == 27 ? 8 : (Q == 19 ? (sizeof(S) == 2 ? XLB_MINB_Q19_16 : 9) : 12));
 };
 
 // Face types, per axis, of the coordinates v - 1, v and v + 1 (periodic) of
@@ -95,7 +98,7 @@ __device__ __forceinline__ uint32_t face_code(const StepParams& p, int x, int y,
     const int ts = (x == 0 ? p.face[0] : 0) | (x == p.nx - 1 ? p.face[1] : 0);    // x
     const int tp = (x == p.nx - 1 ? p.face[0] : 0) | (x == p.nx - 2 ? p.face[1] : 0);  // x + 1
     uint32_t fc = (uint32_t)tm | (uint32_t)ts << 3 | (uint32_t)tp << 6;
-    if (!p.x_linked && (tm | tp) != 0 && (ts == 0 || (FW && ts == FWALL))) fc |= FC_XN;
+    if (!p.x_linked && !p.x_inrow && (tm | tp) != 0 && (ts == 0 || (FW && ts == FWALL))) fc |= FC_XN;
     if (FW && ts == FWALL) fc |= FC_FWALL;
     return fc;
   }
@@ -109,7 +112,7 @@ __device__ __forceinline__ uint32_t face_code(const StepParams& p, int x, int y,
     fc |= (uint32_t)tx[k] << (3 * k) | (uint32_t)ty[k] << (3 * (3 + k)) | (uint32_t)tz[k] << (3 * (6 + k));
   // x-face sources matter to cells that hold state: not to the boundary
   // cells of an x-face plane themselves (FWALL ones do hold state)
-  if (!p.x_linked && (tx[0] | tx[2]) != 0 && (tx[1] == 0 || (FW && tx[1] == FWALL))) fc |= FC_XN;
+  if (!p.x_linked && !p.x_inrow && (tx[0] | tx[2]) != 0 && (tx[1] == 0 || (FW && tx[1] == FWALL))) fc |= FC_XN;
   if ((ty[0] | ty[1] | ty[2] | tz[0] | tz[1] | tz[2]) != 0) fc |= FC_RN;
   const int self = face_combine<FW>(tx[1], ty[1], tz[1]);
   if (self != 0 && face_combine<FW>(0, ty[1], tz[1]) != 0)
@@ -187,6 +190,84 @@ __device__ __forceinline__ void push_ghosts(S* __restrict__ dst, const StepParam
   }
 }
 
+// In-row ghost values of the x-face planes (16-bit storage, p.x_inrow: WALL
+// / LID / EQ faces at both x = 0 and x = nx - 1, no FWALL face).  The cell
+// next to a face, (1, y, z) or (nx - 2, y, z), pulls the directions that
+// cross the face (c_x = +1, resp. -1) from its own row's face cell, (0, y, z)
+// resp. (nx - 1, y, z), instead of from the true source (0, y - c_y, z - c_z)
+// (resp. nx - 1); the face cell holds in slot i the value the true source's
+// rule gives (its type where the planes meet, as face_combine derives it from
+// the row's y / z face types in fc):
+//   WALL: h_opp(i) of the neighbour;  LID: that + 2 w_i rho_w (c_i . u_w) /
+//   cs^2;  EQ: f_i^eq(rho_w, u_w).
+// The bulk pass stores these values with the row, from the neighbour's
+// post-collision values, so the x-faces need no ghost links and the pull no
+// face logic beyond one reload per crossing direction.  Each such slot is
+// read by that one neighbour only; the face cells' other slots are never read.
+template <int Q, bool FW>
+__device__ __forceinline__ float x_inrow_value(const StepParams& p, int i, uint32_t fc, float h_opp) {
+  const int t = face_combine<FW>(p.face[Lattice<Q>::c(i, 0) > 0 ? 0 : 1], fc_type(fc, 1, 1 - Lattice<Q>::c(i, 1)),
+                                 fc_type(fc, 2, 1 - Lattice<Q>::c(i, 2)));
+  return t == EQ ? p.eq_df[i] : h_opp + (t == LID ? p.lid_term[i] : 0.f);
+}
+
+// Plain pull with in-row x-face ghosts: the cells at x = 1 and x = nx - 2
+// take the crossing directions from their own row's face cell.  The address
+// is chosen before the load (a second load into the same value would wait
+// for the first one to land).
+template <int Q, typename S>
+__device__ __forceinline__ void pull_plain_inrow(const S* __restrict__ src, const StepParams& p, const Nbr& nb,
+                                                 int x, float (&df)[Q]) {
+  const bool lo = x == 1, hi = x == p.nx - 2;
+  const S* base = src;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = Lattice<Q>::c(i, 0);
+    const bool cross = Lattice<Q>::c(i, 1) != 0 || Lattice<Q>::c(i, 2) != 0;
+    int s = src_index<Q>(nb, i);
+    if (cx > 0 && cross) s = lo ? nb.xo[0] + nb.rb[1][1] : s;
+    if (cx < 0 && cross) s = hi ? nb.xo[2] + nb.rb[1][1] : s;
+    df[i] = Store<S>::ld(base + s);
+    base += p.plane;
+  }
+}
+
+// The face cells' in-row ghost values in a one-cell-per-thread bulk pass:
+// the lane of x = 0 (x = nx - 1) takes its neighbour's stored h_opp(i) by a
+// shuffle and replaces its own values of the crossing directions, which are
+// then stored with the row.  Called by every lane of a warp that holds a face
+// cell (the rows start warp-aligned, and nx != 1 mod 32 keeps x = nx - 2 in
+// the warp of x = nx - 1).
+template <int Q, typename S, bool FW>
+__device__ __forceinline__ void x_inrow_face_values(const StepParams& p, int x, uint32_t fc, float (&df)[Q],
+                                                    const CellRound<S>& rnd) {
+  const unsigned m = __activemask();
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int cx = Lattice<Q>::c(i, 0);
+    if (cx == 0) continue;
+    const int o = opposite<Q>(i);
+    const float h = rnd.rounded(o, df[o]);
+    const float hn = cx > 0 ? __shfl_down_sync(m, h, 1) : __shfl_up_sync(m, h, 1);
+    if (cx > 0 ? x == 0 : x == p.nx - 1) df[i] = x_inrow_value<Q, FW>(p, i, fc, hn);
+  }
+}
+
+// The same values written from a stored state (after a local collision or a
+// restore) by the neighbour cells, as ghost values.
+template <int Q, typename S, bool FW>
+__device__ __forceinline__ void x_inrow_store(S* __restrict__ f, const StepParams& p, int x, int self, uint32_t fc,
+                                              const float (&hs)[Q], const CellRound<S>& rnd) {
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int cx = Lattice<Q>::c(i, 0);
+    if (cx == 0 || !(cx > 0 ? x == 1 : x == p.nx - 2)) continue;
+    const int o = opposite<Q>(i);
+    const long long slot = (long long)i * p.plane + self - cx;
+    st_ghost<S>(f + slot, (uint32_t)slot, x_inrow_value<Q, FW>(p, i, fc, rnd.rounded(o, hs[o])));
+  }
+}
+
 // Plain periodic pull df_i(x) = h_i(x - c_i) of all Q populations, walking
 // the planes with one pointer (a 64-bit add per plane; a product i * plane
 // per direction costs more instructions).
@@ -214,10 +295,11 @@ __device__ __forceinline__ void store_cell(S* __restrict__ dst, const StepParams
 
 // Which mechanism delivers the rules of the boundary faces to the bulk pass:
 // with 16-bit storage the cells of y / z face rows are skipped and take
-// ghost values pushed by the rows next to them, and only the sources on
-// x-face planes take the rule inside the pull (the kernel is bound by
-// instruction issue: whole warps skip or push, and only the lanes at the ends
-// of a row run face logic); FP32 applies every face rule by coordinates
+// ghost values pushed by the rows next to them, and the sources on x-face
+// planes are in-row ghost values (p.x_inrow), ghost links (p.x_linked) or,
+// with an FWALL x-face, rules inside the pull (the kernel is bound by
+// instruction issue: whole warps skip or push, and at most the lanes at the
+// ends of a row run face logic); FP32 applies every face rule by coordinates
 // inside the pull (the kernel is bound by memory traffic, and the face logic
 // hides under it).  Both give the same pulled values; the readouts, the
 // boundary pass and the adjoint apply the face rules by coordinates and never
@@ -248,7 +330,10 @@ __global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, S, COLL>::value)
     if (fc & FC_SKIP) return;
     Nbr nb;
     make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
-    pull_plain<Q, S>(src, p, nb, df);
+    if (p.x_inrow)
+      pull_plain_inrow<Q, S>(src, p, nb, c.x, df);
+    else
+      pull_plain<Q, S>(src, p, nb, df);
     if (fc & FC_XN) x_face_rules<Q, S, FW>(src, p, c.self, fc, df);
     fwall = (fc & FC_FWALL) != 0u;
   } else {
@@ -263,6 +348,10 @@ __global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, S, COLL>::value)
   CellRound<S> rnd;
   rnd.begin((uint32_t)c.self, df);
   if (GhostFaces<S>::value && (fc & FC_RN)) push_ghosts<Q, S, FW>(dst, p, c.x, c.y, c.z, fc, df, rnd);
+  if (GhostFaces<S>::value && p.x_inrow) {
+    const int wx = c.x & ~31;  // the warp's first x
+    if (wx == 0 || wx == ((p.nx - 1) & ~31)) x_inrow_face_values<Q, S, FW>(p, c.x, fc, df, rnd);
+  }
   store_cell<Q, S>(dst, p, c.self, rnd, df);
 }
 
@@ -274,13 +363,17 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_face_ghosts(S* f, const StepParam
   CellIdx c;
   if (!cell_of_grid(p, c)) return;
   const uint32_t fc = face_code<FW>(p, c.x, c.y, c.z);
-  if (!(fc & FC_RN) || (fc & FC_SKIP)) return;
+  if (fc & FC_SKIP) return;
+  if (p.x_inrow && (c.x == 0 || c.x == p.nx - 1)) return;  // in-row ghost slots only
+  const bool xin = p.x_inrow && (c.x == 1 || c.x == p.nx - 2);
+  if (!(fc & FC_RN) && !xin) return;
   float hs[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) hs[i] = Store<S>::ld_plain(f + (long long)i * p.plane + c.self);
   CellRound<S> rnd;  // the values are stored ones: rounding them again is exact
   rnd.begin((uint32_t)c.self, hs);
-  push_ghosts<Q, S, FW>(f, p, c.x, c.y, c.z, fc, hs, rnd);
+  if (fc & FC_RN) push_ghosts<Q, S, FW>(f, p, c.x, c.y, c.z, fc, hs, rnd);
+  if (xin) x_inrow_store<Q, S, FW>(f, p, c.x, c.self, fc, hs, rnd);
 }
 
 // Ghost value of the link (cell x, direction i) whose source w = x - c_i has
@@ -311,38 +404,6 @@ __device__ __forceinline__ void write_ghost(S* __restrict__ dst, const StepParam
   st_ghost<S>(dst + slot, (uint32_t)slot, v);
 }
 
-// Ghost value of a WALL link with a Bouzidi wall distance q (Bouzidi,
-// Firdaouss and Lallemand 2001; the curved-wall rule Section 4.3 names): the
-// value FLUID cell x pulls in direction j, with hi = h_opp(j)(x):
-//   q <  1/2: 2q hi + (1 - 2q) h_opp(j)(x + c_j)  (hi if x + c_j is not FLUID)
-//   q >= 1/2: hi / (2q) + (1 - 1/(2q)) h_j(x)
-// The cells read are FLUID cells of dst, which the boundary pass never writes.
-template <int Q, typename S>
-__device__ __forceinline__ float bouzidi_ghost(const S* __restrict__ dst, const StepParams& p, int x, int j,
-                                               float hi, float q) {
-  int dx = 0, dy = 0, dz = 0, io = 0;
-#pragma unroll
-  for (int jj = 1; jj < Q; ++jj)
-    if (jj == j) {
-      dx = Lattice<Q>::c(jj, 0);
-      dy = Lattice<Q>::c(jj, 1);
-      dz = Lattice<Q>::c(jj, 2);
-      io = opposite<Q>(jj);
-    }
-  if (q < 0.5f) {
-    const int r = x / p.nx;
-    int bx = x - r * p.nx + dx, by = r % p.ny + dy, bz = r / p.ny + dz;
-    bx = bx < 0 ? p.nx - 1 : (bx >= p.nx ? 0 : bx);
-    by = by < 0 ? p.ny - 1 : (by >= p.ny ? 0 : by);
-    bz = bz < 0 ? p.nz - 1 : (bz >= p.nz ? 0 : bz);
-    const int b = bx + p.nx * (by + p.ny * bz);
-    if ((__ldg(p.flags + b) & FLAG_TYPE) != FLUID) return hi;
-    return 2.0f * q * hi + (1.0f - 2.0f * q) * Store<S>::ld_plain(dst + (long long)io * p.plane + b);
-  }
-  const float inv = 0.5f / q;
-  return inv * hi + (1.0f - inv) * Store<S>::ld_plain(dst + (long long)j * p.plane + x);
-}
-
 // Boundary pass on dst, after a pass that wrote post-collision values there.
 // Threads [0, ceil(n_links / 4)) write the ghost values of the links of FLUID
 // cells and of cells on FWALL face planes (4 links each; LINK_BZ links take
@@ -351,8 +412,8 @@ __device__ __forceinline__ float bouzidi_ghost(const S* __restrict__ dst, const 
 // periodic fluid), by `mode` (FixMode):
 //   FIX_RECOMPUTE:    its update from src with the full rules, stored in dst;
 //   FIX_SIDE_COMPUTE: the same update stored in the side buffer
-//                     side[i * n_fix + k] only (this mode runs beside the
-//                     bulk pass, which it does not depend on);
+//                     side[i * n_fix + k] only (k_fix_recompute; it runs
+//                     beside the bulk pass, which it does not depend on);
 //   FIX_SIDE_COMMIT:  the values of the side buffer stored in dst;
 //   FIX_STORED:       the values already in dst;
 // then (all but FIX_SIDE_COMPUTE) the ghosts of its own links.  src is read
@@ -360,50 +421,11 @@ __device__ __forceinline__ float bouzidi_ghost(const S* __restrict__ dst, const 
 // already in src.
 constexpr int LINKS_PER_THREAD = 4;
 
+// One fix-up cell kf of the boundary pass, by `mode` (see k_boundary).
 template <int Q, typename S, int COLL>
-__global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ src, S* __restrict__ dst,
-                                                        const StepParams p, const int2* __restrict__ links,
-                                                        const float* __restrict__ link_q, int n_links,
-                                                        const int* __restrict__ fix, int n_fix, int mode,
-                                                        S* __restrict__ side) {
-  // link threads: LINKS_PER_THREAD links each, strided by the link-thread
-  // count so that a warp's loads and stores stay on consecutive entries
-  const int n_lt = (n_links + LINKS_PER_THREAD - 1) / LINKS_PER_THREAD;
-  const int k = blockIdx.x * ROW_BLOCK + threadIdx.x;
-  if (k < n_lt) {
-    int2 l[LINKS_PER_THREAD];
-    float h[LINKS_PER_THREAD];
-#pragma unroll
-    for (int m = 0; m < LINKS_PER_THREAD; ++m) {
-      const int e = k + m * n_lt;
-      l[m] = e < n_links ? __ldg(links + e) : make_int2(-1, 0);
-    }
-#pragma unroll
-    for (int m = 0; m < LINKS_PER_THREAD; ++m) {
-      h[m] = 0.f;
-      if (l[m].x >= 0 && ((l[m].y >> 8) & 0xff) != EQ) {
-        int io = 0;
-        const int i = l[m].y & 0xff;
-#pragma unroll
-        for (int j = 1; j < Q; ++j)
-          if (j == i) io = opposite<Q>(j);
-        h[m] = Store<S>::ld_plain(dst + (long long)io * p.plane + l[m].x);
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < LINKS_PER_THREAD; ++m)
-      if (l[m].x >= 0 && (l[m].y & LINK_BZ))
-        h[m] = bouzidi_ghost<Q, S>(dst, p, l[m].x, l[m].y & 0xff, h[m], __ldg(link_q + k + m * n_lt));
-#pragma unroll
-    for (int m = 0; m < LINKS_PER_THREAD; ++m) {
-      if (l[m].x < 0) continue;
-      const int x = l[m].x, r = x / p.nx;
-      write_ghost<Q, S>(dst, p, x - r * p.nx, r % p.ny, r / p.ny, l[m].y & 0xff, (l[m].y >> 8) & 0xff, h[m]);
-    }
-    return;
-  }
-  const int kf = k - n_lt;
-  if (kf >= n_fix) return;
+__device__ __forceinline__ void fix_cell(const S* __restrict__ src, S* __restrict__ dst, const StepParams& p,
+                                         const int* __restrict__ fix, int n_fix, int mode, S* __restrict__ side,
+                                         int kf) {
   const int self = __ldg(fix + kf);
   const int x = self % p.nx;
   const int r = self / p.nx;
@@ -446,11 +468,109 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ sr
 #pragma unroll
     for (int i = 0; i < Q; ++i) df[i] = Store<S>::ld_plain(dst + (long long)i * p.plane + self);
   }
+  // (with in-row x-face ghosts a source on an x-face plane needs none here:
+  // the slot the link would write is the in-row ghost of another row's cell,
+  // and this cell's own pull of it is redone by the recomputation)
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const int t = __ldg(p.flags + src_index<Q>(nb, i)) & FLAG_TYPE;
+    const int sx = x - Lattice<Q>::c(i, 0);
+    if (p.x_inrow && (sx == 0 || sx == p.nx - 1)) continue;
     if (!holds_state(t)) write_ghost<Q, S>(dst, p, x, y, z, i, t, df[opposite<Q>(i)]);
   }
+}
+
+// Ghost value of one link from its precomputed cells (k_link_cells): g.x =
+// the source cell w = x - c_i, whose slot i takes the value; g.y = the
+// Bouzidi partner x + c_i when it is FLUID, else -1.  h = h_opp(i)(x), hb =
+// the Bouzidi partner value; both are FLUID cells of dst, which the boundary
+// pass never writes.
+template <int Q, typename S>
+__device__ __forceinline__ void link_ghost(S* __restrict__ dst, const StepParams& p, int2 l, int2 g, float q,
+                                           float h, float hb) {
+  const int i = l.y & 0xff, t = (l.y >> 8) & 0xff;
+  float add = 0.f, eqv = 0.f;
+#pragma unroll
+  for (int j = 1; j < Q; ++j)
+    if (j == i) {
+      add = p.lid_term[j];
+      eqv = p.eq_df[j];
+    }
+  float v = h;
+  if (l.y & LINK_BZ) {
+    // Bouzidi, Firdaouss and Lallemand (2001), the curved-wall rule Section
+    // 4.3 names, with hi = h_opp(i)(x):
+    //   q <  1/2: 2q hi + (1 - 2q) h_opp(i)(x + c_i)  (hi if x + c_i is not FLUID)
+    //   q >= 1/2: hi / (2q) + (1 - 1/(2q)) h_i(x)
+    if (q < 0.5f) {
+      v = g.y >= 0 ? 2.0f * q * h + (1.0f - 2.0f * q) * hb : h;
+    } else {
+      const float inv = 0.5f / q;
+      v = inv * h + (1.0f - inv) * hb;
+    }
+  }
+  v = t == EQ ? eqv : (t == LID ? v + add : v);
+  const long long slot = (long long)i * p.plane + g.x;
+  st_ghost<S>(dst + slot, (uint32_t)slot, v);
+}
+
+template <int Q, typename S, int COLL>
+__global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ src, S* __restrict__ dst,
+                                                        const StepParams p, const int2* __restrict__ links,
+                                                        const int2* __restrict__ link_cells,
+                                                        const float* __restrict__ link_q, int n_links,
+                                                        const int* __restrict__ fix, int n_fix, int mode,
+                                                        S* __restrict__ side) {
+  // link threads: LINKS_PER_THREAD links each, strided by the link-thread
+  // count so that a warp's loads and stores stay on consecutive entries; all
+  // of a link's reads depend only on its table entries (two rounds of loads)
+  const int n_lt = (n_links + LINKS_PER_THREAD - 1) / LINKS_PER_THREAD;
+  const int k = blockIdx.x * ROW_BLOCK + threadIdx.x;
+  if (k < n_lt) {
+    int2 l[LINKS_PER_THREAD], g[LINKS_PER_THREAD];
+    float q[LINKS_PER_THREAD], h[LINKS_PER_THREAD], hb[LINKS_PER_THREAD];
+#pragma unroll
+    for (int m = 0; m < LINKS_PER_THREAD; ++m) {
+      const int e = k + m * n_lt;
+      const bool ok = e < n_links;
+      l[m] = ok ? __ldg(links + e) : make_int2(-1, 0);
+      g[m] = ok ? __ldg(link_cells + e) : make_int2(0, -1);
+      q[m] = ok && link_q ? __ldg(link_q + e) : 1.0f;
+    }
+#pragma unroll
+    for (int m = 0; m < LINKS_PER_THREAD; ++m) {
+      h[m] = hb[m] = 0.f;
+      if (l[m].x < 0 || ((l[m].y >> 8) & 0xff) == EQ) continue;
+      const int i = l[m].y & 0xff;
+      int io = 0;
+#pragma unroll
+      for (int j = 1; j < Q; ++j)
+        if (j == i) io = opposite<Q>(j);
+      h[m] = Store<S>::ld_plain(dst + (long long)io * p.plane + l[m].x);
+      if (l[m].y & LINK_BZ) {
+        if (q[m] >= 0.5f)
+          hb[m] = Store<S>::ld_plain(dst + (long long)i * p.plane + l[m].x);
+        else if (g[m].y >= 0)
+          hb[m] = Store<S>::ld_plain(dst + (long long)io * p.plane + g[m].y);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < LINKS_PER_THREAD; ++m)
+      if (l[m].x >= 0) link_ghost<Q, S>(dst, p, l[m], g[m], q[m], h[m], hb[m]);
+    return;
+  }
+  const int kf = k - n_lt;
+  if (kf < n_fix) fix_cell<Q, S, COLL>(src, dst, p, fix, n_fix, mode, side, kf);
+}
+
+// The fix-up cells' recomputation into the side buffer (FIX_SIDE_COMPUTE),
+// which runs beside the bulk pass on another stream.
+template <int Q, typename S, int COLL>
+__global__ void __launch_bounds__(ROW_BLOCK) k_fix_recompute(const S* __restrict__ src, const StepParams p,
+                                                             const int* __restrict__ fix, int n_fix,
+                                                             S* __restrict__ side) {
+  const int kf = blockIdx.x * ROW_BLOCK + threadIdx.x;
+  if (kf < n_fix) fix_cell<Q, S, COLL>(src, nullptr, p, fix, n_fix, FIX_SIDE_COMPUTE, side, kf);
 }
 
 // ---------------------------------------------------------------------------
@@ -462,8 +582,10 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_boundary(const S* __restrict__ sr
 // row's) edge loads it from memory, with the periodic wrap.  Faces as for
 // the one-cell kernel with 16-bit storage: the rows of y / z faces are
 // skipped (whole warps) and receive ghost values from the rows next to
-// them; sources on x-face planes take the rule in the lanes at the ends of
-// a row.  Stores are V-wide.  Needs nx % V == 0; no FWALL faces.
+// them; x-faces by in-row ghost values (the threads at the ends of a row
+// hold both the face cell and its neighbour), else by the rule in the lanes
+// at the ends of a row.  Stores are V-wide.  Needs nx % V == 0; no FWALL
+// faces.
 
 template <int Q, typename S, int COLL, int V>
 struct VecMinBlocks {
@@ -503,12 +625,26 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
 #pragma unroll
       for (int c = 0; c < 3; ++c) rb[b][c] = nx * (ys[b] + ny * zs[c]);
   }
+  // in-row x-face ghosts: the thread of x = 0 also holds x = 1, the thread of
+  // x = nx - 1 also holds x = nx - 2 (V >= 2).  With V = 2 those threads load
+  // the crossing directions from their own row (cell 1 takes element 0, cell
+  // nx - 2 element nx - 1; the face cells' own values are not used), and the
+  // lanes next to them load their end element themselves instead of taking
+  // it from the shuffle; with V = 4 the two elements are loaded after the
+  // pull.
+  const bool xin_lo = p.x_inrow && active && x0 == 0, xin_hi = p.x_inrow && active && x0 + V == nx;
+  const bool own_lo = V == 2 && xin_lo, own_hi = V == 2 && xin_hi;
+  const bool post_lo = V == 2 && p.x_inrow && x0 == V, pre_hi = V == 2 && p.x_inrow && x0 + 2 * V == nx;
   float v[Q][V];
   const S* base = src;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = Lattice<Q>::c(i, 0);
-    const S* r = base + rb[1 - Lattice<Q>::c(i, 1)][1 - Lattice<Q>::c(i, 2)];
+    const bool cross = Lattice<Q>::c(i, 1) != 0 || Lattice<Q>::c(i, 2) != 0;
+    int ro = rb[1 - Lattice<Q>::c(i, 1)][1 - Lattice<Q>::c(i, 2)];
+    if (cx == 1 && cross) ro = own_lo ? rb[1][1] : ro;
+    if (cx == -1 && cross) ro = own_hi ? rb[1][1] : ro;
+    const S* r = base + ro;
     float w[V];
     VecIO<S, V>::ld(r + x0, w);
     if (cx == 0) {
@@ -516,16 +652,27 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
       for (int k = 0; k < V; ++k) v[i][k] = w[k];
     } else if (cx == 1) {  // pull from x - 1
       const float up = __shfl_up_sync(0xffffffffu, w[V - 1], 1);
-      v[i][0] = lane > 0 ? up : Store<S>::ld(r + xm);
+      v[i][0] = (lane > 0 && !(cross && post_lo)) ? up : Store<S>::ld(r + xm);
 #pragma unroll
       for (int k = 1; k < V; ++k) v[i][k] = w[k - 1];
     } else {  // pull from x + 1
       const float dn = __shfl_down_sync(0xffffffffu, w[0], 1);
-      v[i][V - 1] = (lane < 31 && !last) ? dn : Store<S>::ld(r + xp);
+      v[i][V - 1] = (lane < 31 && !last && !(cross && pre_hi)) ? dn : Store<S>::ld(r + xp);
 #pragma unroll
       for (int k = 0; k < V - 1; ++k) v[i][k] = w[k + 1];
     }
     base += p.plane;
+  }
+  if (V > 2 && (xin_lo || xin_hi)) {
+    const S* b = src + rb[1][1];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int cx = Lattice<Q>::c(i, 0);
+      const bool cross = Lattice<Q>::c(i, 1) != 0 || Lattice<Q>::c(i, 2) != 0;
+      if (cx == 1 && cross && xin_lo) v[i][1] = Store<S>::ld(b);
+      if (cx == -1 && cross && xin_hi) v[i][V - 2] = Store<S>::ld(b + nx - 1);
+      b += p.plane;
+    }
   }
   const int self0 = x0 + nx * row;
   // sources on x-face planes (only the lanes at the ends of a row have them;
@@ -560,6 +707,17 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
     for (int i = 0; i < Q; ++i) v[i][k] = d[i];
   }
   if (!active) return;
+  if (xin_lo || xin_hi) {
+    uint32_t fr = 0u;  // the row's y / z face types, as face_code packs them
+#pragma unroll
+    for (int a = 0; a < 3; ++a) fr |= (uint32_t)ty[a] << (3 * (3 + a)) | (uint32_t)tz[a] << (3 * (6 + a));
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int cx = Lattice<Q>::c(i, 0), o = opposite<Q>(i);
+      if (cx > 0 && xin_lo) v[i][0] = x_inrow_value<Q, false>(p, i, fr, rnd[1].rounded(o, v[o][1]));
+      if (cx < 0 && xin_hi) v[i][V - 1] = x_inrow_value<Q, false>(p, i, fr, rnd[V - 2].rounded(o, v[o][V - 2]));
+    }
+  }
   // ghost values for the skipped face rows next to this row (from registers,
   // every lane of the row)
   if (p.has_faces && (ty[0] | ty[2] | tz[0] | tz[2]) != 0) {
@@ -886,8 +1044,14 @@ int launch_typed(Op op, const LaunchArgs& a) {
       if (tot <= 0) return 0;
       if (tot > 0x7fffffffLL) return -1;
       const unsigned g = (unsigned)((tot + ROW_BLOCK - 1) / ROW_BLOCK);
-      k_boundary<Q, S, COLL><<<g, ROW_BLOCK, 0, st>>>((const S*)a.src, (S*)a.dst, p, a.links, a.link_q,
-                                                     (int)a.n_links, a.fix, (int)a.n_fix, a.fix_mode,
+      if (a.fix_mode == FIX_SIDE_COMPUTE) {
+        if (a.n_fix <= 0) return 0;
+        k_fix_recompute<Q, S, COLL><<<(unsigned)((a.n_fix + ROW_BLOCK - 1) / ROW_BLOCK), ROW_BLOCK, 0, st>>>(
+            (const S*)a.src, p, a.fix, (int)a.n_fix, (S*)a.side);
+        return 0;
+      }
+      k_boundary<Q, S, COLL><<<g, ROW_BLOCK, 0, st>>>((const S*)a.src, (S*)a.dst, p, a.links, a.link_cells,
+                                                     a.link_q, (int)a.n_links, a.fix, (int)a.n_fix, a.fix_mode,
                                                      (S*)a.side);
       return 0;
     }

@@ -38,6 +38,7 @@ struct LaunchArgs {
   double* partial;
   long long partial_capacity;  // rows of 4 doubles available in partial
   const int2* links;           // OP_BOUNDARY / OP_WALL_FORCE ghost links {cell, dir | type << 8 | flags << 16}
+  const int2* link_cells;      // OP_BOUNDARY: per link {source cell x - c_i, FLUID cell x + c_i or -1}
   const float* link_q;         // Bouzidi wall distance of each LINK_BZ link (or null)
   long long n_links;
   const int* fix;              // OP_BOUNDARY fix-up cells (INLET, OUTLET, FWALL off the faces)
@@ -61,8 +62,9 @@ int launch_d3q27(Op op, const LaunchArgs& a);
 // Number of blocks the row-mapped kernels launch for a lattice (partials).
 long long row_blocks(const StepParams& p);
 
-// Mask preparation: validates codes (< 7), writes flag bytes; err_word is set
-// to 1 on an invalid code.  Q picks the stencil used for the FLAG_SLOW test.
+// Mask preparation: validates codes (< 7), writes flag bytes; err_word[0] is
+// set to 1 on an invalid code, err_word[2] where an INLET, OUTLET or FWALL
+// cell occurs.  Q picks the stencil used for the FLAG_SLOW test.
 int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int ny, int nz, int* err_word,
                         void* stream);
 int launch_reduce_final(const double* partial, long long n, double* out, void* stream);
@@ -82,5 +84,9 @@ int launch_pred_count(int mode, int dir, int Q, const int* face, const uint8_t* 
                       int* counts, void* stream);
 int launch_pred_write(int mode, int dir, int Q, const int* face, const uint8_t* flags, int nx, int ny, int nz,
                       const long long* offs, int2* links, int* cells, void* stream);
+// Per link {cell x, dir i | ...}: the source cell x - c_i (periodic) and the
+// cell x + c_i when it is FLUID, else -1 (the boundary pass's Bouzidi partner).
+int launch_link_cells(int Q, const int2* links, long long n, const uint8_t* flags, int nx, int ny, int nz,
+                      int2* cells, void* stream);
 
 }  // namespace xlb

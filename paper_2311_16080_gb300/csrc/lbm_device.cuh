@@ -56,6 +56,35 @@ __device__ __forceinline__ void moments(const float (&df)[Q], float& drho, float
   }
 }
 
+// Moments of order 0, 1 and 2 of the deviations in one pass over the pairs
+// (i, opp(i)): their sum carries the even moments, their difference the odd.
+// M = sum_i c_ia c_ib df_i, stored xx yy zz xy xz yz.
+template <int Q>
+__device__ __forceinline__ void moments_kbc(const float (&df)[Q], float& drho, float (&j)[3], float (&M)[6]) {
+  drho = df[0];
+  j[0] = j[1] = j[2] = 0.f;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) M[a] = 0.f;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    if (opposite<Q>(i) > i) {
+      const float sp = df[i] + df[opposite<Q>(i)], dm = df[i] - df[opposite<Q>(i)];
+      constexpr int D = Lattice<Q>::D;
+      const int cx = Lattice<Q>::c(i, 0), cy = Lattice<Q>::c(i, 1), cz = D == 3 ? Lattice<Q>::c(i, 2) : 0;
+      drho += sp;
+      if (cx) j[0] += cx * dm;
+      if (cy) j[1] += cy * dm;
+      if (cz) j[2] += cz * dm;
+      if (cx) M[0] += sp;
+      if (cy) M[1] += sp;
+      if (cz) M[2] += sp;
+      if (cx * cy) M[3] += (float)(cx * cy) * sp;
+      if (cx * cz) M[4] += (float)(cx * cz) * sp;
+      if (cy * cz) M[5] += (float)(cy * cz) * sp;
+    }
+  }
+}
+
 // Bracket of Eq. 5 without the leading 1: 3 c.u + 4.5 (c.u)^2 - 1.5 u.u
 template <int Q>
 __device__ __forceinline__ float eq_poly(int i, const float (&u)[3], float usq) {
@@ -123,15 +152,26 @@ __device__ __forceinline__ bool pull_periodic(const S* __restrict__ src, const S
   bool near = false;
   if (p.has_faces) {
     const int xs[3] = {nb.xo[0], x, nb.xo[2]};
-    const int ys[3] = {wrap_m(y, p.ny), y, wrap_p(y, p.ny)};
-    const int zs[3] = {p.nz > 1 ? wrap_m(z, p.nz) : 0, z, p.nz > 1 ? wrap_p(z, p.nz) : 0};
+    if (y > 1 && y < p.ny - 2 && (p.nz == 1 || (z > 1 && z < p.nz - 2))) {
+      // a row two or more planes from the y / z face planes (uniform over a
+      // warp) can only meet x-faces
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int cx = face_code(xs[k], p.nx), cy = face_code(ys[k], p.ny), cz = face_code(zs[k], p.nz);
-      fcx[k] = (cx & 1 ? p.face[0] : 0) | (cx & 2 ? p.face[1] : 0);
-      fcy[k] = (cy & 1 ? p.face[2] : 0) | (cy & 2 ? p.face[3] : 0);
-      fcz[k] = p.nz > 1 ? ((cz & 1 ? p.face[4] : 0) | (cz & 2 ? p.face[5] : 0)) : 0;
-      near |= (k != 1 || FW) && (fcx[k] | fcy[k] | fcz[k]);
+      for (int k = 0; k < 3; ++k) {
+        const int cx = face_code(xs[k], p.nx);
+        fcx[k] = (cx & 1 ? p.face[0] : 0) | (cx & 2 ? p.face[1] : 0);
+        near |= (k != 1 || FW) && fcx[k];
+      }
+    } else {
+      const int ys[3] = {wrap_m(y, p.ny), y, wrap_p(y, p.ny)};
+      const int zs[3] = {p.nz > 1 ? wrap_m(z, p.nz) : 0, z, p.nz > 1 ? wrap_p(z, p.nz) : 0};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int cx = face_code(xs[k], p.nx), cy = face_code(ys[k], p.ny), cz = face_code(zs[k], p.nz);
+        fcx[k] = (cx & 1 ? p.face[0] : 0) | (cx & 2 ? p.face[1] : 0);
+        fcy[k] = (cy & 1 ? p.face[2] : 0) | (cy & 2 ? p.face[3] : 0);
+        fcz[k] = p.nz > 1 ? ((cz & 1 ? p.face[4] : 0) | (cz & 2 ? p.face[5] : 0)) : 0;
+        near |= (k != 1 || FW) && (fcx[k] | fcy[k] | fcz[k]);
+      }
     }
   }
   const S* base = src;
@@ -350,8 +390,11 @@ __device__ __forceinline__ float kbc_ds(int i, const float (&hd)[3], const float
 template <int Q, int COLL>
 __device__ __forceinline__ void collide(float (&df)[Q], const StepParams& p) {
   if (COLL == COLL_NONE) return;
-  float drho, j[3];
-  moments<Q>(df, drho, j);
+  float drho, j[3], M[6];
+  if (COLL == COLL_KBC)
+    moments_kbc<Q>(df, drho, j, M);
+  else
+    moments<Q>(df, drho, j);
   const float rho = 1.0f + drho;
   const float ir = 1.0f / rho;
   float u[3] = {j[0] * ir, j[1] * ir, j[2] * ir};
@@ -378,50 +421,45 @@ __device__ __forceinline__ void collide(float (&df)[Q], const StepParams& p) {
       }
     }
   } else {
-    // KBC.  Only f^neq stays live; the equilibrium terms and ds are cheap to
-    // recompute.  With dh = f^neq - ds the update reads
+    // KBC.  The second moments of f^neq come from those of the deviations
+    // (moments_kbc) and the closed form of the equilibrium's: on these
+    // lattices sum_i c_ia c_ib f_i^eq = rho (d_ab / 3 + u_a u_b), so
+    //   P_ab = M_ab - rho u_a u_b - d_ab drho / 3.
+    // One pass then turns df into f^neq and forms <ds|dh> and <dh|dh>, with
+    // dh = f^neq - ds; with them the update reads
     //   df_i <- df_i^eq + (1 - beta gamma) f^neq_i - beta (2 - gamma) ds_i.
-    float fneq[Q];
-    float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx yy zz xy xz yz
-    fneq[0] = df[0] - weight<Q>(0) * (drho + rho * b0);
+    constexpr float third = 1.0f / 3.0f;
+    const float dd = drho * third;
+    const float P0 = M[0] - rho * u[0] * u[0] - dd, P1 = M[1] - rho * u[1] * u[1] - dd;
+    const float P2 = Lattice<Q>::D == 3 ? M[2] - rho * u[2] * u[2] - dd : 0.f;
+    constexpr float inv_d = 1.0f / Lattice<Q>::D;
+    const float tr = (P0 + P1 + P2) * inv_d;
+    // ds_i: D_aa / 2 on the axis directions, c_a c_b Pi_ab / 4 on the two-component ones
+    const float hd[3] = {0.5f * (P0 - tr), 0.5f * (P1 - tr), 0.5f * (P2 - tr)};
+    const float qo[3] = {0.25f * (M[3] - rho * u[0] * u[1]), 0.25f * (M[4] - rho * u[0] * u[2]),
+                         0.25f * (M[5] - rho * u[1] * u[2])};
+    // <a|b> = sum a_i b_i / f_i^eq with f_i^eq = w_i rho (1 + b +- a); the
+    // common 1/rho cancels in gamma, and one reciprocal serves a pair:
+    // 1 / (X +- a) = (X -+ a) / (X^2 - a^2).  The rest direction has ds = 0.
+    df[0] -= weight<Q>(0) * (drho + rho * b0);
+    float hh = df[0] * df[0] * __fdividef(1.0f / weight<Q>(0), 1.0f + b0), sh = 0.f;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       if (opposite<Q>(i) > i) {
         const int j = opposite<Q>(i);
         const float cu = cdot<Q>(i, u);
         const float w = weight<Q>(i);
-        const float bb = drho + rho * fmaf(4.5f * cu, cu, b0), ra = rho * 3.0f * cu;
-        const float fi = df[i] - w * (bb + ra), fj = df[j] - w * (bb - ra);
-        fneq[i] = fi;
-        fneq[j] = fj;
-        const float sp = fi + fj;  // second moments are even in c
-        if (Lattice<Q>::c(i, 0)) P[0] += sp;
-        if (Lattice<Q>::c(i, 1)) P[1] += sp;
-        if (Lattice<Q>::c(i, 2)) P[2] += sp;
-        if (Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 1)) P[3] += (float)(Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 1)) * sp;
-        if (Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 2)) P[4] += (float)(Lattice<Q>::c(i, 0) * Lattice<Q>::c(i, 2)) * sp;
-        if (Lattice<Q>::c(i, 1) * Lattice<Q>::c(i, 2)) P[5] += (float)(Lattice<Q>::c(i, 1) * Lattice<Q>::c(i, 2)) * sp;
-      }
-    }
-    constexpr float inv_d = 1.0f / Lattice<Q>::D;
-    const float tr = P[0] + P[1] + P[2];
-    // ds_i: D_aa / 2 on the axis directions, c_a c_b Pi_ab / 4 on the two-component ones
-    const float hd[3] = {0.5f * (P[0] - tr * inv_d), 0.5f * (P[1] - tr * inv_d), 0.5f * (P[2] - tr * inv_d)};
-    const float qo[3] = {0.25f * P[3], 0.25f * P[4], 0.25f * P[5]};
-    // <a|b> = sum a_i b_i / f_i^eq with f_i^eq = w_i rho (1 + b +- a); the
-    // common 1/rho cancels in gamma.  The rest direction has ds = 0.
-    float hh = fneq[0] * fneq[0] * __fdividef(1.0f / weight<Q>(0), 1.0f + b0), sh = 0.f;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      if (opposite<Q>(i) > i) {
-        const int j = opposite<Q>(i);
-        const float s_ = kbc_ds<Q>(i, hd, qo);
-        const float cu = cdot<Q>(i, u);
         const float bq = fmaf(4.5f * cu, cu, b0), a3 = 3.0f * cu;
-        const float iw = 1.0f / weight<Q>(i);
-        const float ri = __fdividef(iw, 1.0f + bq + a3), rj = __fdividef(iw, 1.0f + bq - a3);
-        const float hi = fneq[i] - s_, hj = fneq[j] - s_;
-        sh = fmaf(s_, fmaf(hi, ri, hj * rj), sh);
+        const float bb = drho + rho * bq, ra = rho * a3;
+        const float fi = df[i] - w * (bb + ra), fj = df[j] - w * (bb - ra);
+        df[i] = fi;
+        df[j] = fj;
+        const float X = 1.0f + bq;
+        const float rc = __fdividef(1.0f / w, fmaf(X, X, -a3 * a3));
+        const float ri = (X - a3) * rc, rj = (X + a3) * rc;
+        const float s_ = kbc_ds<Q>(i, hd, qo);
+        const float hi = fi - s_, hj = fj - s_;
+        if (nnz<Q>(i) < 3) sh = fmaf(s_, fmaf(hi, ri, hj * rj), sh);
         hh = fmaf(hi * hi, ri, fmaf(hj * hj, rj, hh));
       }
     }
@@ -429,7 +467,7 @@ __device__ __forceinline__ void collide(float (&df)[Q], const StepParams& p) {
     const float ib = 1.0f / beta;
     const float gamma = (hh < 1e-20f * rho) ? 2.0f : ib - (2.0f - ib) * sh / hh;
     const float a1 = 1.0f - beta * gamma, a2 = beta * (2.0f - gamma);
-    df[0] = weight<Q>(0) * (drho + rho * b0) + a1 * fneq[0];
+    df[0] = fmaf(a1, df[0], weight<Q>(0) * (drho + rho * b0));
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       if (opposite<Q>(i) > i) {
@@ -438,8 +476,8 @@ __device__ __forceinline__ void collide(float (&df)[Q], const StepParams& p) {
         const float w = weight<Q>(i);
         const float bb = drho + rho * fmaf(4.5f * cu, cu, b0), ra = rho * 3.0f * cu;
         const float sd = a2 * kbc_ds<Q>(i, hd, qo);
-        df[i] = w * (bb + ra) + a1 * fneq[i] - sd;
-        df[j] = w * (bb - ra) + a1 * fneq[j] - sd;
+        df[i] = fmaf(w, bb + ra, fmaf(a1, df[i], -sd));
+        df[j] = fmaf(w, bb - ra, fmaf(a1, df[j], -sd));
       }
     }
   }

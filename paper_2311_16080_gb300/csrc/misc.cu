@@ -12,13 +12,30 @@ long long row_blocks(const StepParams& p) {
   return nxb * (long long)p.ny * p.nz;
 }
 
+// Coordinates of a cell index; 32-bit divisions where the lattice allows.
+__device__ __forceinline__ void cell_xyz(long long cell, int nx, int ny, bool small, int& x, int& y, int& z) {
+  if (small) {
+    const unsigned c = (unsigned)cell, r = c / (unsigned)nx;
+    x = (int)(c - r * (unsigned)nx);
+    y = (int)(r % (unsigned)ny);
+    z = (int)(r / (unsigned)ny);
+  } else {
+    const long long r = cell / nx;
+    x = (int)(cell - r * nx);
+    y = (int)(r % ny);
+    z = (int)(r / ny);
+  }
+}
+
 // flags = type | FLAG_SLOW where a fluid-like cell has a WALL / LID / EQ cell
 // in its Q-stencil, or is an INLET / OUTLET / FWALL cell.  Codes >= 7 set
-// *err.
+// err[0]; an INLET, OUTLET or FWALL cell anywhere sets err[2].
 template <int Q>
 __global__ void k_mask_prepare(const uint8_t* __restrict__ mask, uint8_t* __restrict__ flags, int nx, int ny,
                                int nz, int* err) {
   const long long n = (long long)nx * ny * nz;
+  const bool small = n < 0x7fffffffLL;
+  bool io = false;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
        cell += (long long)gridDim.x * blockDim.x) {
     const int t = mask[cell];
@@ -28,11 +45,10 @@ __global__ void k_mask_prepare(const uint8_t* __restrict__ mask, uint8_t* __rest
       continue;
     }
     int slow = (t == INLET || t == OUTLET || t == FWALL);
+    io |= slow != 0;
     if (fluid_like(t) && !slow) {
-      const int x = (int)(cell % nx);
-      const long long r = cell / nx;
-      const int y = (int)(r % ny);
-      const int z = (int)(r / ny);
+      int x, y, z;
+      cell_xyz(cell, nx, ny, small, x, y, z);
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         int xs = x - Lattice<Q>::c(i, 0), ys = y - Lattice<Q>::c(i, 1), zs = z - Lattice<Q>::c(i, 2);
@@ -45,6 +61,7 @@ __global__ void k_mask_prepare(const uint8_t* __restrict__ mask, uint8_t* __rest
     }
     flags[cell] = (uint8_t)(t | (slow ? FLAG_SLOW : 0));
   }
+  if (io) atomicOr(err + 2, 1);
 }
 
 int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int ny, int nz, int* err,
@@ -91,11 +108,12 @@ __device__ __forceinline__ bool on_face_plane(int x, int y, int z, int nx, int n
 
 __device__ __forceinline__ int pred_eval(const uint8_t* __restrict__ flags, long long cell, int nx, int ny, int nz,
                                          const Pred& pr, int* type) {
-  const int t = flags[cell] & FLAG_TYPE;
+  const int fl = flags[cell];
+  const int t = fl & FLAG_TYPE;
   if (pr.mode == 1 ? !(t == INLET || t == OUTLET || t == FWALL) : !(t == FLUID || t == FWALL)) return 0;
-  const int x = (int)(cell % nx);
-  const long long r = cell / nx;
-  const int y = (int)(r % ny), z = (int)(r / ny);
+  if (!(fl & FLAG_SLOW)) return 0;  // a FLUID cell with no WALL / LID / EQ source
+  int x, y, z;
+  cell_xyz(cell, nx, ny, (long long)nx * ny * nz < 0x7fffffffLL, x, y, z);
   // an FWALL cell on a face plane is updated by the bulk pass (it lies on an
   // FWALL face: the host keeps a face only where its plane's cells have the
   // type the faces derive); any other FWALL cell is a fix-up cell
@@ -192,6 +210,47 @@ int launch_pred_write(int mode, int dir, int Q, const int* face, const uint8_t* 
   const Pred pr = make_pred(mode, dir, Q, face);
   k_pred_write<<<(unsigned)b, LIST_BLOCK, 0, (cudaStream_t)stream>>>(flags, n, nx, ny, nz, pr, dir, offs, links,
                                                                      cells);
+  return 0;
+}
+
+template <int Q>
+__global__ void k_link_cells(const int2* __restrict__ links, long long n, const uint8_t* __restrict__ flags,
+                             int nx, int ny, int nz, int2* __restrict__ cells) {
+  const bool small = (long long)nx * ny * nz < 0x7fffffffLL;
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n; e += (long long)gridDim.x * 256) {
+    const int2 l = links[e];
+    const int i = l.y & 0xff;
+    int cx = 0, cy = 0, cz = 0;
+#pragma unroll
+    for (int j = 1; j < Q; ++j)
+      if (j == i) {
+        cx = Lattice<Q>::c(j, 0);
+        cy = Lattice<Q>::c(j, 1);
+        cz = Lattice<Q>::c(j, 2);
+      }
+    int x, y, z;
+    cell_xyz(l.x, nx, ny, small, x, y, z);
+    auto wrap = [](int v, int m) { return v < 0 ? m - 1 : (v >= m ? 0 : v); };
+    const int w = wrap(x - cx, nx) + nx * (wrap(y - cy, ny) + ny * wrap(z - cz, nz));
+    const int b = wrap(x + cx, nx) + nx * (wrap(y + cy, ny) + ny * wrap(z + cz, nz));
+    cells[e] = make_int2(w, (flags[b] & FLAG_TYPE) == FLUID ? b : -1);
+  }
+}
+
+int launch_link_cells(int Q, const int2* links, long long n, const uint8_t* flags, int nx, int ny, int nz,
+                      int2* cells, void* stream) {
+  if (n <= 0) return 0;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152LL * 32) blocks = 152LL * 32;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (Q == 9)
+    k_link_cells<9><<<(unsigned)blocks, 256, 0, s>>>(links, n, flags, nx, ny, nz, cells);
+  else if (Q == 19)
+    k_link_cells<19><<<(unsigned)blocks, 256, 0, s>>>(links, n, flags, nx, ny, nz, cells);
+  else if (Q == 27)
+    k_link_cells<27><<<(unsigned)blocks, 256, 0, s>>>(links, n, flags, nx, ny, nz, cells);
+  else
+    return -1;
   return 0;
 }
 

@@ -1,9 +1,11 @@
 """Bulk-pass variants and the boundary tables.
 
-The two bulk variants (one cell per thread, and four cells per thread with
-vector loads and warp shuffles) give identical populations; the boundary
-tables (ghost links and inlet / outlet cells) have the sizes the mask fixes;
-ghost values follow changes of the lid velocity and of the mask mid-run.
+The bulk variants (one cell per thread, and two or four cells per thread
+with vector loads and warp shuffles) give identical populations; the
+boundary tables (ghost links and inlet / outlet cells) have the sizes the
+mask fixes; the two forms of the 16-bit x-faces (in-row ghost values, ghost
+links) and the fix-up cells beside them agree with the oracle; ghost values
+follow changes of the lid velocity and of the mask mid-run.
 """
 import numpy as np
 import pytest
@@ -37,6 +39,32 @@ def _cases():
     m[-1, :] = O.WALL
     r, u = I.random_flow(sh, 2, seed=8, rho_amp=0.005, u_amp=0.02)
     out.append(("fwall9", Case(9, sh, 1.4, "bgk", mask=m, force=(1e-5, 0.0, 0.0), rho0=r, u0=u)))
+    # x-face planes of the other two types: EQ at x = 0, a tangentially moving
+    # LID at x = nx - 1, meeting WALL rows; interior obstacles, some beside
+    # the x-faces
+    sh = (36, 64)
+    m = np.zeros(sh, np.uint8)
+    m[:, 0] = O.EQ
+    m[:, -1] = O.LID
+    m[0, :] = O.WALL
+    m[-1, :] = O.WALL
+    obst = I.random_obstacle_mask(sh, 0.05, seed=11) > 0
+    obst[[0, -1], :] = False
+    obst[:, [0, -1]] = False
+    m[obst] = O.WALL
+    r, u = I.random_flow(sh, 2, seed=12, rho_amp=0.005, u_amp=0.02)
+    out.append(("xfaces9", Case(9, sh, 1.5, "bgk", mask=m, force=(0.0, 1e-5, 0.0), lid=(1.0, (0.0, 0.03, 0.0)),
+                                eq=(1.0, (0.02, 0.01, 0.0)), rho0=r, u0=u)))
+    # D3Q19: EQ x = 0 face, LID x = nx - 1 face moving along z, WALL y faces,
+    # periodic in z; 40 / 4 = 10 slots per row (a partial warp)
+    m = np.zeros((10, 12, 40), np.uint8)
+    m[:, :, 0] = O.EQ
+    m[:, :, -1] = O.LID
+    m[:, 0, :] = O.WALL
+    m[:, -1, :] = O.WALL
+    r, u = I.random_flow(m.shape, 3, seed=13, rho_amp=0.005, u_amp=0.02)
+    out.append(("xfaces19", Case(19, m.shape, 1.6, "bgk", mask=m, lid=(1.0, (0.0, 0.0, 0.03)),
+                                 eq=(1.0, (0.02, 0.0, 0.01)), rho0=r, u0=u)))
     return out
 
 
@@ -118,18 +146,68 @@ def test_auto_picks_the_variant_by_storage():
         s.close()
 
 
-def test_16_bit_x_faces_are_served_by_ghost_links():
-    """With 16-bit storage the WALL / LID / EQ x-face planes are boundary
-    links (the bulk pass then runs no face logic at the ends of a row); the
-    y / z faces stay faces.  FP32 keeps all six faces."""
+def _one_x_face_cavity():
+    """The cavity with its x = nx - 1 plane opened (fluid inside the y / z
+    face planes, the lid running through to the edge): only the x = 0 face
+    remains."""
     m = I.lid_driven_cavity_mask(20, 18, 16)
-    want16 = _links(19, m, [(1, 0), (1, -1), (0, 0), (0, -1)])
-    assert want16 > 0
-    for st, want in (("f32", 0), ("f16", want16), ("bf16", want16)):
-        s = X.Simulation(19, (20, 18, 16), 1.5, "bgk", st)
-        s.set_mask(m)
-        assert X.xlb_boundary_links(s.ctx) == (want, 0)
-        s.close()
+    m[1:-1, 1:-1, -1] = O.FLUID
+    m[-1, 1:-1, -1] = O.LID
+    return m
+
+
+def test_16_bit_x_faces_in_row_or_linked():
+    """With 16-bit storage WALL / LID / EQ x-faces at both ends are served by
+    in-row ghost values (no links); with only one x-face, or where the cells
+    x = nx - 2 and nx - 1 fall in different warps (nx = 1 mod 32), their
+    sources are ghost links.  The y / z faces stay faces; FP32 keeps all six."""
+    yz = [(1, 0), (1, -1), (0, 0), (0, -1)]
+    m20 = I.lid_driven_cavity_mask(20, 18, 16)
+    m33 = I.lid_driven_cavity_mask(33, 10, 9)
+    one = _one_x_face_cavity()
+    w33 = _links(19, m33, yz)
+    w_one = _links(19, one, yz)
+    assert w33 > 0 and w_one > 0
+    w32_one = _links(19, one, yz + [(2, 0)])  # FP32: the x = 0 face stays a face
+    for m, w16, w32 in ((m20, 0, 0), (m33, w33, 0), (one, w_one, w32_one)):
+        for st in ("f32", "f16", "bf16"):
+            s = X.Simulation(19, tuple(reversed(m.shape)), 1.5, "bgk", st)
+            s.set_mask(m)
+            assert X.xlb_boundary_links(s.ctx) == (w32 if st == "f32" else w16, 0), (m.shape, st)
+            s.close()
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("kind", ["nx33", "one_face"])
+def test_linked_x_faces_match_oracle(storage, kind):
+    """The ghost-link form of the 16-bit x-faces (one cell per thread)
+    against the oracle, at the storage bound."""
+    m = I.lid_driven_cavity_mask(33, 10, 9) if kind == "nx33" else _one_x_face_cavity()
+    r, u = I.random_flow(m.shape, 3, seed=14, rho_amp=0.005, u_amp=0.02)
+    c = Case(19, m.shape, 1.6, "bgk", mask=m, lid=(1.0, (0.05, 0.0, 0.0)), rho0=r, u0=u)
+    (_, u_o), _ = c.oracle(100)
+    _, u_g = c.gpu(100, storage)
+    fl = O.fluid_like(m)
+    assert rel_l2(u_g[:, fl], u_o[:, fl]) <= 5e-3
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_inlet_cells_beside_in_row_x_faces(storage):
+    """INLET and OUTLET segments in the columns next to WALL x-faces: their
+    recomputation must not write the x-face slots, which hold the in-row
+    ghost values of the fluid cells around the segments."""
+    sh = (40, 64)
+    m = I.channel_2d_mask(64, 40)
+    m[:, 0] = O.WALL
+    m[:, -1] = O.WALL
+    m[12:25, 1] = O.INLET
+    m[8:30, -2] = O.OUTLET
+    r, u = I.random_flow(sh, 2, seed=15, rho_amp=0.005, u_amp=0.02)
+    c = Case(9, sh, 1.5, "bgk", mask=m, inlet=(0.03, 0.0, 0.0), rho0=r, u0=u)
+    (_, u_o), _ = c.oracle(150)
+    _, u_g = c.gpu(150, storage)
+    fl = O.fluid_like(m)
+    assert rel_l2(u_g[:, fl], u_o[:, fl]) <= (1e-4 if storage == "f32" else 5e-3)
 
 
 def _links(q, m, skip_faces=()):
