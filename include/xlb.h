@@ -124,10 +124,11 @@ int xlb_set_mask(xlb_ctx* ctx, const uint8_t* mask);
 
 /* Sizes of the boundary tables of the current mask.  Whole face planes that
  * the mask fills with one boundary type are handled by coordinates and need
- * no table.  With 16-bit storage, WALL / LID / EQ x-face planes at both
- * x = 0 and x = nx - 1 (no FWALL face) are served by in-row ghost values
- * that the bulk pass stores in each row's face cells; with only one such
- * x-face, or with nx = 1 (mod 32), their sources are table entries.
+ * no table (with 16-bit storage the WALL / LID / EQ planes x = 0 and
+ * x = nx - 1 are served by the table instead).  Whole INLET planes at x = 0
+ * and OUTLET planes at x = nx - 1 (apart from cells on y / z faces) are
+ * updated by the bulk pass; their cells then count as link owners, not as
+ * fix-up cells.
  * n_links = number of (cell, direction) pairs, over FLUID cells
  * and FWALL cells of FWALL face planes, whose source cell is WALL, LID or EQ
  * off the face planes; n_fix = number of INLET and OUTLET cells plus the

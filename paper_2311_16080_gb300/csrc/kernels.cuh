@@ -98,7 +98,7 @@ __device__ __forceinline__ uint32_t face_code(const StepParams& p, int x, int y,
     const int ts = (x == 0 ? p.face[0] : 0) | (x == p.nx - 1 ? p.face[1] : 0);    // x
     const int tp = (x == p.nx - 1 ? p.face[0] : 0) | (x == p.nx - 2 ? p.face[1] : 0);  // x + 1
     uint32_t fc = (uint32_t)tm | (uint32_t)ts << 3 | (uint32_t)tp << 6;
-    if (!p.x_linked && !p.x_inrow && (tm | tp) != 0 && (ts == 0 || (FW && ts == FWALL))) fc |= FC_XN;
+    if (!p.x_linked && (tm | tp) != 0 && (ts == 0 || (FW && ts == FWALL))) fc |= FC_XN;
     if (FW && ts == FWALL) fc |= FC_FWALL;
     return fc;
   }
@@ -112,7 +112,7 @@ __device__ __forceinline__ uint32_t face_code(const StepParams& p, int x, int y,
     fc |= (uint32_t)tx[k] << (3 * k) | (uint32_t)ty[k] << (3 * (3 + k)) | (uint32_t)tz[k] << (3 * (6 + k));
   // x-face sources matter to cells that hold state: not to the boundary
   // cells of an x-face plane themselves (FWALL ones do hold state)
-  if (!p.x_linked && !p.x_inrow && (tx[0] | tx[2]) != 0 && (tx[1] == 0 || (FW && tx[1] == FWALL))) fc |= FC_XN;
+  if (!p.x_linked && (tx[0] | tx[2]) != 0 && (tx[1] == 0 || (FW && tx[1] == FWALL))) fc |= FC_XN;
   if ((ty[0] | ty[1] | ty[2] | tz[0] | tz[1] | tz[2]) != 0) fc |= FC_RN;
   const int self = face_combine<FW>(tx[1], ty[1], tz[1]);
   if (self != 0 && face_combine<FW>(0, ty[1], tz[1]) != 0)
@@ -190,84 +190,6 @@ __device__ __forceinline__ void push_ghosts(S* __restrict__ dst, const StepParam
   }
 }
 
-// In-row ghost values of the x-face planes (16-bit storage, p.x_inrow: WALL
-// / LID / EQ faces at both x = 0 and x = nx - 1, no FWALL face).  The cell
-// next to a face, (1, y, z) or (nx - 2, y, z), pulls the directions that
-// cross the face (c_x = +1, resp. -1) from its own row's face cell, (0, y, z)
-// resp. (nx - 1, y, z), instead of from the true source (0, y - c_y, z - c_z)
-// (resp. nx - 1); the face cell holds in slot i the value the true source's
-// rule gives (its type where the planes meet, as face_combine derives it from
-// the row's y / z face types in fc):
-//   WALL: h_opp(i) of the neighbour;  LID: that + 2 w_i rho_w (c_i . u_w) /
-//   cs^2;  EQ: f_i^eq(rho_w, u_w).
-// The bulk pass stores these values with the row, from the neighbour's
-// post-collision values, so the x-faces need no ghost links and the pull no
-// face logic beyond one reload per crossing direction.  Each such slot is
-// read by that one neighbour only; the face cells' other slots are never read.
-template <int Q, bool FW>
-__device__ __forceinline__ float x_inrow_value(const StepParams& p, int i, uint32_t fc, float h_opp) {
-  const int t = face_combine<FW>(p.face[Lattice<Q>::c(i, 0) > 0 ? 0 : 1], fc_type(fc, 1, 1 - Lattice<Q>::c(i, 1)),
-                                 fc_type(fc, 2, 1 - Lattice<Q>::c(i, 2)));
-  return t == EQ ? p.eq_df[i] : h_opp + (t == LID ? p.lid_term[i] : 0.f);
-}
-
-// Plain pull with in-row x-face ghosts: the cells at x = 1 and x = nx - 2
-// take the crossing directions from their own row's face cell.  The address
-// is chosen before the load (a second load into the same value would wait
-// for the first one to land).
-template <int Q, typename S>
-__device__ __forceinline__ void pull_plain_inrow(const S* __restrict__ src, const StepParams& p, const Nbr& nb,
-                                                 int x, float (&df)[Q]) {
-  const bool lo = x == 1, hi = x == p.nx - 2;
-  const S* base = src;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int cx = Lattice<Q>::c(i, 0);
-    const bool cross = Lattice<Q>::c(i, 1) != 0 || Lattice<Q>::c(i, 2) != 0;
-    int s = src_index<Q>(nb, i);
-    if (cx > 0 && cross) s = lo ? nb.xo[0] + nb.rb[1][1] : s;
-    if (cx < 0 && cross) s = hi ? nb.xo[2] + nb.rb[1][1] : s;
-    df[i] = Store<S>::ld(base + s);
-    base += p.plane;
-  }
-}
-
-// The face cells' in-row ghost values in a one-cell-per-thread bulk pass:
-// the lane of x = 0 (x = nx - 1) takes its neighbour's stored h_opp(i) by a
-// shuffle and replaces its own values of the crossing directions, which are
-// then stored with the row.  Called by every lane of a warp that holds a face
-// cell (the rows start warp-aligned, and nx != 1 mod 32 keeps x = nx - 2 in
-// the warp of x = nx - 1).
-template <int Q, typename S, bool FW>
-__device__ __forceinline__ void x_inrow_face_values(const StepParams& p, int x, uint32_t fc, float (&df)[Q],
-                                                    const CellRound<S>& rnd) {
-  const unsigned m = __activemask();
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const int cx = Lattice<Q>::c(i, 0);
-    if (cx == 0) continue;
-    const int o = opposite<Q>(i);
-    const float h = rnd.rounded(o, df[o]);
-    const float hn = cx > 0 ? __shfl_down_sync(m, h, 1) : __shfl_up_sync(m, h, 1);
-    if (cx > 0 ? x == 0 : x == p.nx - 1) df[i] = x_inrow_value<Q, FW>(p, i, fc, hn);
-  }
-}
-
-// The same values written from a stored state (after a local collision or a
-// restore) by the neighbour cells, as ghost values.
-template <int Q, typename S, bool FW>
-__device__ __forceinline__ void x_inrow_store(S* __restrict__ f, const StepParams& p, int x, int self, uint32_t fc,
-                                              const float (&hs)[Q], const CellRound<S>& rnd) {
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const int cx = Lattice<Q>::c(i, 0);
-    if (cx == 0 || !(cx > 0 ? x == 1 : x == p.nx - 2)) continue;
-    const int o = opposite<Q>(i);
-    const long long slot = (long long)i * p.plane + self - cx;
-    st_ghost<S>(f + slot, (uint32_t)slot, x_inrow_value<Q, FW>(p, i, fc, rnd.rounded(o, hs[o])));
-  }
-}
-
 // Plain periodic pull df_i(x) = h_i(x - c_i) of all Q populations, walking
 // the planes with one pointer (a 64-bit add per plane; a product i * plane
 // per direction costs more instructions).
@@ -296,10 +218,10 @@ __device__ __forceinline__ void store_cell(S* __restrict__ dst, const StepParams
 // Which mechanism delivers the rules of the boundary faces to the bulk pass:
 // with 16-bit storage the cells of y / z face rows are skipped and take
 // ghost values pushed by the rows next to them, and the sources on x-face
-// planes are in-row ghost values (p.x_inrow), ghost links (p.x_linked) or,
-// with an FWALL x-face, rules inside the pull (the kernel is bound by
-// instruction issue: whole warps skip or push, and at most the lanes at the
-// ends of a row run face logic); FP32 applies every face rule by coordinates
+// planes are ghost links (p.x_linked) or, with an FWALL x-face, take the
+// rules inside the pull (the kernel is bound by instruction issue: whole
+// warps skip or push, and at most the lanes at the ends of a row run face
+// logic); FP32 applies every face rule by coordinates
 // inside the pull (the kernel is bound by memory traffic, and the face logic
 // hides under it).  Both give the same pulled values; the readouts, the
 // boundary pass and the adjoint apply the face rules by coordinates and never
@@ -317,7 +239,7 @@ struct GhostFaces {
 // GhostFaces describes; cells on FWALL face planes reverse instead of
 // colliding (FW).  Other boundary cells get values nobody reads until
 // k_boundary rewrites them; inlet / outlet cells are recomputed there too.
-template <int Q, typename S, int COLL, bool FW>
+template <int Q, typename S, int COLL, bool FW, bool IO = false>
 __global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, S, COLL>::value)
     k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, const StepParams p) {
   CellIdx c;
@@ -325,22 +247,27 @@ __global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, S, COLL>::value)
   float df[Q];
   uint32_t fc = 0u;
   bool fwall = false;
+  // IO (a separate instance, so that the other lattices keep their register
+  // budget): an OUTLET plane at x = nx - 1 served here copies the pull of
+  // x - 1 in the directions c_x = -1, whose sources x - 1 - c_i lie in its
+  // own column; an INLET plane at x = 0 takes the inlet rule
+  const bool outl = IO && p.x_outlet && c.x == p.nx - 1;
   if constexpr (GhostFaces<S>::value) {
     fc = face_code<FW>(p, c.x, c.y, c.z);
     if (fc & FC_SKIP) return;
     Nbr nb;
     make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
-    if (p.x_inrow)
-      pull_plain_inrow<Q, S>(src, p, nb, c.x, df);
-    else
-      pull_plain<Q, S>(src, p, nb, df);
+    if (outl) nb.xo[2] = c.x;
+    pull_plain<Q, S>(src, p, nb, df);
     if (fc & FC_XN) x_face_rules<Q, S, FW>(src, p, c.self, fc, df);
     fwall = (fc & FC_FWALL) != 0u;
   } else {
     Nbr nb;
     make_nbr(nb, c.x, c.y, c.z, p.nx, p.ny, p.nz);
-    fwall = pull_periodic<Q, S, FW>(src, p, nb, c.self, c.x, c.y, c.z, df);
+    if (outl) nb.xo[2] = c.x;
+    fwall = pull_periodic<Q, S, FW>(src, p, nb, c.self, c.x, c.y, c.z, df, outl);
   }
+  if (IO && p.x_inlet && c.x == 0) inlet_rule<Q>(p, c.self, df);
   if (FW && COLL != COLL_NONE && fwall)
     reverse_populations<Q>(df);
   else
@@ -348,10 +275,6 @@ __global__ void __launch_bounds__(ROW_BLOCK, MinBlocks<Q, S, COLL>::value)
   CellRound<S> rnd;
   rnd.begin((uint32_t)c.self, df);
   if (GhostFaces<S>::value && (fc & FC_RN)) push_ghosts<Q, S, FW>(dst, p, c.x, c.y, c.z, fc, df, rnd);
-  if (GhostFaces<S>::value && p.x_inrow) {
-    const int wx = c.x & ~31;  // the warp's first x
-    if (wx == 0 || wx == ((p.nx - 1) & ~31)) x_inrow_face_values<Q, S, FW>(p, c.x, fc, df, rnd);
-  }
   store_cell<Q, S>(dst, p, c.self, rnd, df);
 }
 
@@ -363,17 +286,13 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_face_ghosts(S* f, const StepParam
   CellIdx c;
   if (!cell_of_grid(p, c)) return;
   const uint32_t fc = face_code<FW>(p, c.x, c.y, c.z);
-  if (fc & FC_SKIP) return;
-  if (p.x_inrow && (c.x == 0 || c.x == p.nx - 1)) return;  // in-row ghost slots only
-  const bool xin = p.x_inrow && (c.x == 1 || c.x == p.nx - 2);
-  if (!(fc & FC_RN) && !xin) return;
+  if (!(fc & FC_RN) || (fc & FC_SKIP)) return;
   float hs[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) hs[i] = Store<S>::ld_plain(f + (long long)i * p.plane + c.self);
   CellRound<S> rnd;  // the values are stored ones: rounding them again is exact
   rnd.begin((uint32_t)c.self, hs);
-  if (fc & FC_RN) push_ghosts<Q, S, FW>(f, p, c.x, c.y, c.z, fc, hs, rnd);
-  if (xin) x_inrow_store<Q, S, FW>(f, p, c.x, c.self, fc, hs, rnd);
+  push_ghosts<Q, S, FW>(f, p, c.x, c.y, c.z, fc, hs, rnd);
 }
 
 // Ghost value of the link (cell x, direction i) whose source w = x - c_i has
@@ -468,14 +387,9 @@ __device__ __forceinline__ void fix_cell(const S* __restrict__ src, S* __restric
 #pragma unroll
     for (int i = 0; i < Q; ++i) df[i] = Store<S>::ld_plain(dst + (long long)i * p.plane + self);
   }
-  // (with in-row x-face ghosts a source on an x-face plane needs none here:
-  // the slot the link would write is the in-row ghost of another row's cell,
-  // and this cell's own pull of it is redone by the recomputation)
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const int t = __ldg(p.flags + src_index<Q>(nb, i)) & FLAG_TYPE;
-    const int sx = x - Lattice<Q>::c(i, 0);
-    if (p.x_inrow && (sx == 0 || sx == p.nx - 1)) continue;
     if (!holds_state(t)) write_ghost<Q, S>(dst, p, x, y, z, i, t, df[opposite<Q>(i)]);
   }
 }
@@ -582,10 +496,9 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_fix_recompute(const S* __restrict
 // row's) edge loads it from memory, with the periodic wrap.  Faces as for
 // the one-cell kernel with 16-bit storage: the rows of y / z faces are
 // skipped (whole warps) and receive ghost values from the rows next to
-// them; x-faces by in-row ghost values (the threads at the ends of a row
-// hold both the face cell and its neighbour), else by the rule in the lanes
-// at the ends of a row.  Stores are V-wide.  Needs nx % V == 0; no FWALL
-// faces.
+// them; sources on x-face planes are ghost links (16-bit storage) or take
+// the rule in the lanes at the ends of a row.  Stores are V-wide.  Needs
+// nx % V == 0; no FWALL faces.
 
 template <int Q, typename S, int COLL, int V>
 struct VecMinBlocks {
@@ -615,7 +528,10 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
   }
   const bool last = !active || x0 + V >= nx;  // no active right neighbour lane
   const int xm = x0 == 0 ? nx - 1 : x0 - 1;    // element left of the vector
-  const int xp = x0 + V >= nx ? 0 : x0 + V;    // element right of the vector
+  // element right of the vector; an OUTLET plane at x = nx - 1 served here
+  // copies the pull of x - 1 in the directions c_x = -1, whose sources lie in
+  // its own column
+  const int xp = x0 + V >= nx ? (p.x_outlet ? nx - 1 : 0) : x0 + V;
   int rb[3][3];
   {
     const int ys[3] = {wrap_m(y, ny), y, wrap_p(y, ny)};
@@ -625,26 +541,12 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
 #pragma unroll
       for (int c = 0; c < 3; ++c) rb[b][c] = nx * (ys[b] + ny * zs[c]);
   }
-  // in-row x-face ghosts: the thread of x = 0 also holds x = 1, the thread of
-  // x = nx - 1 also holds x = nx - 2 (V >= 2).  With V = 2 those threads load
-  // the crossing directions from their own row (cell 1 takes element 0, cell
-  // nx - 2 element nx - 1; the face cells' own values are not used), and the
-  // lanes next to them load their end element themselves instead of taking
-  // it from the shuffle; with V = 4 the two elements are loaded after the
-  // pull.
-  const bool xin_lo = p.x_inrow && active && x0 == 0, xin_hi = p.x_inrow && active && x0 + V == nx;
-  const bool own_lo = V == 2 && xin_lo, own_hi = V == 2 && xin_hi;
-  const bool post_lo = V == 2 && p.x_inrow && x0 == V, pre_hi = V == 2 && p.x_inrow && x0 + 2 * V == nx;
   float v[Q][V];
   const S* base = src;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = Lattice<Q>::c(i, 0);
-    const bool cross = Lattice<Q>::c(i, 1) != 0 || Lattice<Q>::c(i, 2) != 0;
-    int ro = rb[1 - Lattice<Q>::c(i, 1)][1 - Lattice<Q>::c(i, 2)];
-    if (cx == 1 && cross) ro = own_lo ? rb[1][1] : ro;
-    if (cx == -1 && cross) ro = own_hi ? rb[1][1] : ro;
-    const S* r = base + ro;
+    const S* r = base + rb[1 - Lattice<Q>::c(i, 1)][1 - Lattice<Q>::c(i, 2)];
     float w[V];
     VecIO<S, V>::ld(r + x0, w);
     if (cx == 0) {
@@ -652,29 +554,27 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
       for (int k = 0; k < V; ++k) v[i][k] = w[k];
     } else if (cx == 1) {  // pull from x - 1
       const float up = __shfl_up_sync(0xffffffffu, w[V - 1], 1);
-      v[i][0] = (lane > 0 && !(cross && post_lo)) ? up : Store<S>::ld(r + xm);
+      v[i][0] = lane > 0 ? up : Store<S>::ld(r + xm);
 #pragma unroll
       for (int k = 1; k < V; ++k) v[i][k] = w[k - 1];
     } else {  // pull from x + 1
       const float dn = __shfl_down_sync(0xffffffffu, w[0], 1);
-      v[i][V - 1] = (lane < 31 && !last && !(cross && pre_hi)) ? dn : Store<S>::ld(r + xp);
+      v[i][V - 1] = (lane < 31 && !last) ? dn : Store<S>::ld(r + xp);
 #pragma unroll
       for (int k = 0; k < V - 1; ++k) v[i][k] = w[k + 1];
     }
     base += p.plane;
   }
-  if (V > 2 && (xin_lo || xin_hi)) {
-    const S* b = src + rb[1][1];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int cx = Lattice<Q>::c(i, 0);
-      const bool cross = Lattice<Q>::c(i, 1) != 0 || Lattice<Q>::c(i, 2) != 0;
-      if (cx == 1 && cross && xin_lo) v[i][1] = Store<S>::ld(b);
-      if (cx == -1 && cross && xin_hi) v[i][V - 2] = Store<S>::ld(b + nx - 1);
-      b += p.plane;
-    }
-  }
   const int self0 = x0 + nx * row;
+  // an INLET plane at x = 0 served here
+  if (p.x_inlet && active && x0 == 0) {
+    float d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = v[i][0];
+    inlet_rule<Q>(p, self0, d);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i][0] = d[i];
+  }
   // sources on x-face planes (only the lanes at the ends of a row have them;
   // none when ghost links serve them)
   if (p.has_faces && !p.x_linked && (x0 <= 1 || x0 + V >= nx - 1)) {
@@ -707,17 +607,6 @@ __global__ void __launch_bounds__(128, VecMinBlocks<Q, S, COLL, V>::value)
     for (int i = 0; i < Q; ++i) v[i][k] = d[i];
   }
   if (!active) return;
-  if (xin_lo || xin_hi) {
-    uint32_t fr = 0u;  // the row's y / z face types, as face_code packs them
-#pragma unroll
-    for (int a = 0; a < 3; ++a) fr |= (uint32_t)ty[a] << (3 * (3 + a)) | (uint32_t)tz[a] << (3 * (6 + a));
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int cx = Lattice<Q>::c(i, 0), o = opposite<Q>(i);
-      if (cx > 0 && xin_lo) v[i][0] = x_inrow_value<Q, false>(p, i, fr, rnd[1].rounded(o, v[o][1]));
-      if (cx < 0 && xin_hi) v[i][V - 1] = x_inrow_value<Q, false>(p, i, fr, rnd[V - 2].rounded(o, v[o][V - 2]));
-    }
-  }
   // ghost values for the skipped face rows next to this row (from registers,
   // every lane of the row)
   if (p.has_faces && (ty[0] | ty[2] | tz[0] | tz[2]) != 0) {
@@ -1017,6 +906,8 @@ int launch_typed(Op op, const LaunchArgs& a) {
       }
       if (fw)
         k_stream_collide<Q, S, COLL, true><<<g3, block, 0, st>>>((const S*)a.src, (S*)a.dst, q);
+      else if (p.x_inlet || p.x_outlet)
+        k_stream_collide<Q, S, COLL, false, true><<<g3, block, 0, st>>>((const S*)a.src, (S*)a.dst, q);
       else
         k_stream_collide<Q, S, COLL, false><<<g3, block, 0, st>>>((const S*)a.src, (S*)a.dst, q);
       return 0;

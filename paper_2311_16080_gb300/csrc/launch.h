@@ -80,10 +80,13 @@ long long launch_sum_squares(const float* x, long long n, double* partial, long 
 long long bnd_list_blocks(long long n);
 // `face` (6 types, or null) lists the described boundary faces: links whose
 // source lies on one are left out (the pull applies those rules itself).
-int launch_pred_count(int mode, int dir, int Q, const int* face, const uint8_t* flags, int nx, int ny, int nz,
-                      int* counts, void* stream);
-int launch_pred_write(int mode, int dir, int Q, const int* face, const uint8_t* flags, int nx, int ny, int nz,
-                      const long long* offs, int2* links, int* cells, void* stream);
+// x_in / x_out: the INLET cells of x = 0 / OUTLET cells of x = nx - 1 are
+// served by the bulk pass: they are not fix-up cells, and their links are
+// listed like those of FLUID cells.
+int launch_pred_count(int mode, int dir, int Q, const int* face, bool x_in, bool x_out, const uint8_t* flags, int nx,
+                      int ny, int nz, int* counts, void* stream);
+int launch_pred_write(int mode, int dir, int Q, const int* face, bool x_in, bool x_out, const uint8_t* flags, int nx,
+                      int ny, int nz, const long long* offs, int2* links, int* cells, void* stream);
 // Per link {cell x, dir i | ...}: the source cell x - c_i (periodic) and the
 // cell x + c_i when it is FLUID, else -1 (the boundary pass's Bouzidi partner).
 int launch_link_cells(int Q, const int2* links, long long n, const uint8_t* flags, int nx, int ny, int nz,

@@ -145,9 +145,12 @@ __device__ __forceinline__ void reverse_populations(float (&df)[Q]) {
 // Returns, with FW, whether the cell itself lies on an FWALL face plane (its
 // own coordinates then count as near a face, so that only warps holding such
 // cells evaluate it).
+// With `outlet` (a cell of an OUTLET plane x = nx - 1 that copies the pull of
+// x - 1 in the directions c_x = -1, nb.xo[2] then being x itself) the face
+// rules of those directions take the populations of x - 1.
 template <int Q, typename S, bool FW = true>
 __device__ __forceinline__ bool pull_periodic(const S* __restrict__ src, const StepParams& p, const Nbr& nb,
-                                              int self, int x, int y, int z, float (&df)[Q]) {
+                                              int self, int x, int y, int z, float (&df)[Q], bool outlet = false) {
   int fcx[3] = {0, 0, 0}, fcy[3] = {0, 0, 0}, fcz[3] = {0, 0, 0};
   bool near = false;
   if (p.has_faces) {
@@ -193,7 +196,8 @@ __device__ __forceinline__ bool pull_periodic(const S* __restrict__ src, const S
     const int t = i == 0 ? 0
                          : face_combine<FW>(fcx[1 - Lattice<Q>::c(i, 0)], fcy[1 - Lattice<Q>::c(i, 1)],
                                             fcz[1 - Lattice<Q>::c(i, 2)]);
-    const S* a = t ? src + (long long)opposite<Q>(i) * p.plane + self : base + src_index<Q>(nb, i);
+    const int own = (Lattice<Q>::c(i, 0) == -1 && outlet) ? self - 1 : self;
+    const S* a = t ? src + (long long)opposite<Q>(i) * p.plane + own : base + src_index<Q>(nb, i);
     df[i] = Store<S>::ld(a);
     base += p.plane;
   }
@@ -308,6 +312,15 @@ __device__ __forceinline__ void regularized_inlet(const StepParams& p, int self,
   }
 }
 
+// The velocity boundary of an INLET cell, by the chosen scheme.
+template <int Q>
+__device__ __forceinline__ void inlet_rule(const StepParams& p, int self, float (&df)[Q]) {
+  if (p.inlet_regularized)
+    regularized_inlet<Q>(p, self, df);
+  else
+    zou_he_inlet<Q>(p, self, df);
+}
+
 // Post-stream populations of a fluid-like or FWALL cell.  The pull applies
 // the face rules and reads the ghost values that every other WALL / LID / EQ
 // source carries (see k_boundary), i.e. the bounce-back, moving-wall and
@@ -319,12 +332,7 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ src, const StepP
                                           int type, const Nbr& nb, float (&df)[Q]) {
   const int self = x + p.nx * (y + p.ny * z);
   pull_periodic<Q, S>(src, p, nb, self, x, y, z, df);
-  if (type == INLET) {
-    if (p.inlet_regularized)
-      regularized_inlet<Q>(p, self, df);
-    else
-      zou_he_inlet<Q>(p, self, df);
-  }
+  if (type == INLET) inlet_rule<Q>(p, self, df);
   if (type == OUTLET) {
     const int xl = wrap_m(x, p.nx);
     Nbr nl;

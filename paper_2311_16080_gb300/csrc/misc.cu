@@ -85,19 +85,21 @@ int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int 
 // Boundary tables, built once per mask by compaction in two passes per
 // table (per-block counts; an exclusive scan of the counts on the host; then
 // ordered per-block writes):
-//  - links, direction-major: for each direction i in turn, every FLUID cell
-//    and every FWALL cell on an FWALL face plane x (ascending) whose source
-//    x - c_i is WALL, LID or EQ and not on a face plane, as
-//    {x, i | type << 8}.  Consecutive entries then touch consecutive cells of
-//    one population plane wherever the wall is not normal to x;
-//  - fix-up cells: every INLET and OUTLET cell and every FWALL cell off the
-//    face planes, ascending.
+//  - links, direction-major: for each direction i in turn, every FLUID cell,
+//    every FWALL cell on an FWALL face plane and every inlet / outlet cell the
+//    bulk pass serves, x (ascending), whose source x - c_i is WALL, LID or EQ
+//    and not on a face plane, as {x, i | type << 8}.  Consecutive entries
+//    then touch consecutive cells of one population plane wherever the wall
+//    is not normal to x;
+//  - fix-up cells: every other INLET and OUTLET cell and every FWALL cell off
+//    the face planes, ascending.
 constexpr int LIST_BLOCK = 256;
 
 struct Pred {
   int mode;        // 0: link in direction (cx, cy, cz); 1: fix-up cell
   int cx, cy, cz;  // velocity of the link direction
   int face[6];     // described boundary faces: their sources need no ghost
+  int x_in, x_out; // INLET cells of x = 0 / OUTLET cells of x = nx - 1 served by the bulk pass
 };
 
 // Does (x, y, z) lie on one of the described face planes?
@@ -110,15 +112,19 @@ __device__ __forceinline__ int pred_eval(const uint8_t* __restrict__ flags, long
                                          const Pred& pr, int* type) {
   const int fl = flags[cell];
   const int t = fl & FLAG_TYPE;
-  if (pr.mode == 1 ? !(t == INLET || t == OUTLET || t == FWALL) : !(t == FLUID || t == FWALL)) return 0;
+  if (!(t == FLUID || t == FWALL || t == INLET || t == OUTLET)) return 0;
+  if (pr.mode == 1 && t == FLUID) return 0;
   if (!(fl & FLAG_SLOW)) return 0;  // a FLUID cell with no WALL / LID / EQ source
   int x, y, z;
   cell_xyz(cell, nx, ny, (long long)nx * ny * nz < 0x7fffffffLL, x, y, z);
+  // inlet / outlet cells on the x-planes the bulk pass serves
+  const bool io_bulk = (t == INLET && pr.x_in && x == 0) || (t == OUTLET && pr.x_out && x == nx - 1);
+  if (pr.mode == 0 && (t == INLET || t == OUTLET) && !io_bulk) return 0;
   // an FWALL cell on a face plane is updated by the bulk pass (it lies on an
   // FWALL face: the host keeps a face only where its plane's cells have the
   // type the faces derive); any other FWALL cell is a fix-up cell
   const bool fw_face = t == FWALL && on_face_plane(x, y, z, nx, ny, nz, pr);
-  if (pr.mode == 1) return t == INLET || t == OUTLET || (t == FWALL && !fw_face);
+  if (pr.mode == 1) return ((t == INLET || t == OUTLET) && !io_bulk) || (t == FWALL && !fw_face);
   if (t == FWALL && !fw_face) return 0;
   int xs = x - pr.cx, ys = y - pr.cy, zs = z - pr.cz;
   xs = xs < 0 ? nx - 1 : (xs >= nx ? 0 : xs);
@@ -168,9 +174,11 @@ __global__ void k_pred_write(const uint8_t* __restrict__ flags, long long n, int
 
 long long bnd_list_blocks(long long n) { return (n + LIST_BLOCK - 1) / LIST_BLOCK; }
 
-static Pred make_pred(int mode, int dir, int Q, const int* face) {
+static Pred make_pred(int mode, int dir, int Q, const int* face, bool x_in, bool x_out) {
   Pred pr;
   pr.mode = mode;
+  pr.x_in = x_in ? 1 : 0;
+  pr.x_out = x_out ? 1 : 0;
   pr.cx = pr.cy = pr.cz = 0;
   for (int f = 0; f < 6; ++f) pr.face[f] = face ? face[f] : 0;
   if (mode == 0) {
@@ -192,22 +200,22 @@ static Pred make_pred(int mode, int dir, int Q, const int* face) {
   return pr;
 }
 
-int launch_pred_count(int mode, int dir, int Q, const int* face, const uint8_t* flags, int nx, int ny, int nz,
-                      int* counts, void* stream) {
+int launch_pred_count(int mode, int dir, int Q, const int* face, bool x_in, bool x_out, const uint8_t* flags, int nx,
+                      int ny, int nz, int* counts, void* stream) {
   const long long n = (long long)nx * ny * nz;
   const long long b = bnd_list_blocks(n);
   if (b > 0x7fffffffLL) return -1;
-  const Pred pr = make_pred(mode, dir, Q, face);
+  const Pred pr = make_pred(mode, dir, Q, face, x_in, x_out);
   k_pred_count<<<(unsigned)b, LIST_BLOCK, 0, (cudaStream_t)stream>>>(flags, n, nx, ny, nz, pr, counts);
   return 0;
 }
 
-int launch_pred_write(int mode, int dir, int Q, const int* face, const uint8_t* flags, int nx, int ny, int nz,
-                      const long long* offs, int2* links, int* cells, void* stream) {
+int launch_pred_write(int mode, int dir, int Q, const int* face, bool x_in, bool x_out, const uint8_t* flags, int nx,
+                      int ny, int nz, const long long* offs, int2* links, int* cells, void* stream) {
   const long long n = (long long)nx * ny * nz;
   const long long b = bnd_list_blocks(n);
   if (b > 0x7fffffffLL) return -1;
-  const Pred pr = make_pred(mode, dir, Q, face);
+  const Pred pr = make_pred(mode, dir, Q, face, x_in, x_out);
   k_pred_write<<<(unsigned)b, LIST_BLOCK, 0, (cudaStream_t)stream>>>(flags, n, nx, ny, nz, pr, dir, offs, links,
                                                                      cells);
   return 0;

@@ -56,11 +56,13 @@ struct StepParams {
   int face[6];
   int has_faces;
   // 16-bit bulk passes: the sources on the x-face planes outside the skipped
-  // y / z face rows are served by ghost links (x_linked), or by in-row ghost
-  // values that the face cell of each row holds for its neighbour (x_inrow),
-  // instead of by rules in the pull
+  // y / z face rows are served by ghost links, not by rules in the pull
   int x_linked;
-  int x_inrow;
+  // the x = 0 plane is INLET / the x = nx - 1 plane is OUTLET (outside the
+  // y / z face planes): the bulk pass applies the inlet rule / the outflow
+  // copy in the lanes of those cells, which are not fix-up cells
+  int x_inlet;
+  int x_outlet;
   // bulk kernels: 1 when launched on a (x-blocks, ny, nz) grid, 0 when the
   // grid is flattened over rows (ny or nz above the grid limit)
   int grid3;

@@ -3,9 +3,9 @@
 The bulk variants (one cell per thread, and two or four cells per thread
 with vector loads and warp shuffles) give identical populations; the
 boundary tables (ghost links and inlet / outlet cells) have the sizes the
-mask fixes; the two forms of the 16-bit x-faces (in-row ghost values, ghost
-links) and the fix-up cells beside them agree with the oracle; ghost values
-follow changes of the lid velocity and of the mask mid-run.
+mask fixes; the 16-bit x-face links, the fix-up cells beside them and the
+inflow / outflow planes that the bulk pass serves agree with the oracle;
+ghost values follow changes of the lid velocity and of the mask mid-run.
 """
 import numpy as np
 import pytest
@@ -55,6 +55,18 @@ def _cases():
     r, u = I.random_flow(sh, 2, seed=12, rho_amp=0.005, u_amp=0.02)
     out.append(("xfaces9", Case(9, sh, 1.5, "bgk", mask=m, force=(0.0, 1e-5, 0.0), lid=(1.0, (0.0, 0.03, 0.0)),
                                 eq=(1.0, (0.02, 0.01, 0.0)), rho0=r, u0=u)))
+    # inflow / outflow planes served by the bulk pass: D2Q9 channel, INLET
+    # column x = 0 (Zou-He), OUTLET column x = nx - 1, WALL rows, obstacles
+    sh = (34, 96)
+    m = I.channel_2d_mask(96, 34)
+    m[1:-1, 0] = O.INLET
+    m[1:-1, -1] = O.OUTLET
+    obst = I.random_obstacle_mask(sh, 0.03, seed=16) > 0
+    obst[[0, -1], :] = False
+    obst[:, [0, 1, -2, -1]] = False
+    m[obst] = O.WALL
+    r, u = I.random_flow(sh, 2, seed=17, rho_amp=0.005, u_amp=0.02)
+    out.append(("inout9", Case(9, sh, 1.5, "bgk", mask=m, inlet=(0.03, 0.0, 0.0), rho0=r, u0=u)))
     # D3Q19: EQ x = 0 face, LID x = nx - 1 face moving along z, WALL y faces,
     # periodic in z; 40 / 4 = 10 slots per row (a partial warp)
     m = np.zeros((10, 12, 40), np.uint8)
@@ -156,20 +168,18 @@ def _one_x_face_cavity():
     return m
 
 
-def test_16_bit_x_faces_in_row_or_linked():
-    """With 16-bit storage WALL / LID / EQ x-faces at both ends are served by
-    in-row ghost values (no links); with only one x-face, or where the cells
-    x = nx - 2 and nx - 1 fall in different warps (nx = 1 mod 32), their
-    sources are ghost links.  The y / z faces stay faces; FP32 keeps all six."""
+def test_16_bit_x_faces_are_served_by_ghost_links():
+    """With 16-bit storage the sources on WALL / LID / EQ x-face planes are
+    ghost links (the bulk pass then runs no face logic at the ends of a row);
+    the y / z faces stay faces.  FP32 keeps all six faces."""
     yz = [(1, 0), (1, -1), (0, 0), (0, -1)]
     m20 = I.lid_driven_cavity_mask(20, 18, 16)
     m33 = I.lid_driven_cavity_mask(33, 10, 9)
     one = _one_x_face_cavity()
-    w33 = _links(19, m33, yz)
-    w_one = _links(19, one, yz)
-    assert w33 > 0 and w_one > 0
     w32_one = _links(19, one, yz + [(2, 0)])  # FP32: the x = 0 face stays a face
-    for m, w16, w32 in ((m20, 0, 0), (m33, w33, 0), (one, w_one, w32_one)):
+    for m, w32 in ((m20, 0), (m33, 0), (one, w32_one)):
+        w16 = _links(19, m, yz)
+        assert w16 > 0
         for st in ("f32", "f16", "bf16"):
             s = X.Simulation(19, tuple(reversed(m.shape)), 1.5, "bgk", st)
             s.set_mask(m)
@@ -180,8 +190,9 @@ def test_16_bit_x_faces_in_row_or_linked():
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 @pytest.mark.parametrize("kind", ["nx33", "one_face"])
 def test_linked_x_faces_match_oracle(storage, kind):
-    """The ghost-link form of the 16-bit x-faces (one cell per thread)
-    against the oracle, at the storage bound."""
+    """The ghost links of the 16-bit x-faces with an odd nx (one cell per
+    thread) and with a single x-face, against the oracle, at the storage
+    bound."""
     m = I.lid_driven_cavity_mask(33, 10, 9) if kind == "nx33" else _one_x_face_cavity()
     r, u = I.random_flow(m.shape, 3, seed=14, rho_amp=0.005, u_amp=0.02)
     c = Case(19, m.shape, 1.6, "bgk", mask=m, lid=(1.0, (0.05, 0.0, 0.0)), rho0=r, u0=u)
@@ -192,10 +203,10 @@ def test_linked_x_faces_match_oracle(storage, kind):
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
-def test_inlet_cells_beside_in_row_x_faces(storage):
-    """INLET and OUTLET segments in the columns next to WALL x-faces: their
-    recomputation must not write the x-face slots, which hold the in-row
-    ghost values of the fluid cells around the segments."""
+def test_inlet_cells_beside_x_faces(storage):
+    """INLET and OUTLET segments in the columns next to WALL x-faces (fix-up
+    cells, whose boundary links sit beside the x-face ghost links of the
+    fluid cells around the segments), against the oracle."""
     sh = (40, 64)
     m = I.channel_2d_mask(64, 40)
     m[:, 0] = O.WALL
@@ -210,8 +221,15 @@ def test_inlet_cells_beside_in_row_x_faces(storage):
     assert rel_l2(u_g[:, fl], u_o[:, fl]) <= (1e-4 if storage == "f32" else 5e-3)
 
 
-def _links(q, m, skip_faces=()):
+def _links(q, m, skip_faces=(), io_owners=False, owner_mask=None):
+    """Ghost links: (owner cell, direction) with a WALL / LID / EQ source off
+    the listed face planes; owners are FLUID cells and, with io_owners, the
+    inflow / outflow cells the bulk pass serves (owner_mask, else all INLET
+    and OUTLET cells)."""
     lat = O.Lattice(q)
+    owners = m == O.FLUID
+    if io_owners:
+        owners = owners | (owner_mask if owner_mask is not None else np.isin(m, (O.INLET, O.OUTLET)))
     n = 0
     for i in range(1, q):
         src_nonfluid = ~O.fluid_like(lat.roll(m, i))
@@ -225,7 +243,7 @@ def _links(q, m, skip_faces=()):
             sh = [1] * m.ndim
             sh[ax] = m.shape[ax]
             on_face |= hit.reshape(sh)
-        n += int(((m == O.FLUID) & src_nonfluid & ~on_face).sum())
+        n += int((owners & src_nonfluid & ~on_face).sum())
     return n
 
 
@@ -242,12 +260,21 @@ def test_boundary_tables():
     # the hole removes the x = 0 face; the lid plane's x = 0 edge cells are
     # WALL, which only the x = 0 face explained, so the lid face goes too
     holed_faces = [f for f in all_faces if f not in ((2, 0), (0, -1))]
-    for q, m, faces in ((19, cav, all_faces), (19, holed, holed_faces),
-                        (27, sph, []), (9, eqs, [])):
-        want = (_links(q, m, faces), int(np.isin(m, (O.INLET, O.OUTLET)).sum()))
+    seg = I.channel_2d_mask(40, 30)
+    seg[10:20, 0] = O.INLET  # a segment: its cells stay fix-up cells
+    seg[1:-1, -1] = O.OUTLET
+    seg[12:15, 1:3] = O.WALL  # an obstacle touching the inlet segment
+    for q, m, faces, planes in ((19, cav, all_faces, False), (19, holed, holed_faces, False),
+                                (27, sph, [], True), (9, eqs, [], False), (9, seg, [(0, 0), (0, -1)], False)):
+        # the whole INLET plane x = 0 / OUTLET plane x = nx - 1 of the sphere
+        # channel is served by the bulk pass: no fix-up cells, links owned
+        io = np.isin(m, (O.INLET, O.OUTLET))
+        want = (_links(q, m, faces, io_owners=planes), 0 if planes else int(io.sum()))
+        if m is seg:  # the outlet column is a whole plane, the inlet segment is not
+            want = (_links(q, m, faces, io_owners=True, owner_mask=(m == O.OUTLET)), int((m == O.INLET).sum()))
         s = X.Simulation(q, tuple(reversed(m.shape)), 1.5, "bgk")
         s.set_mask(m)
-        assert X.xlb_boundary_links(s.ctx) == want
+        assert X.xlb_boundary_links(s.ctx) == want, (m.shape, want)
         s.close()
     assert _links(19, cav, all_faces) == 0
 
