@@ -417,16 +417,25 @@ static int launch_init(xlb_ctx* c, void* dst) {
   return dispatch(c, OP_INIT, a);
 }
 
-// Boundary faces of a mask (host copy): a face plane qualifies when none of
+// The six boundary planes of a mask, gathered on the device into one compact
+// host buffer (the x-planes are strided in the mask): plane f (x = 0,
+// x = nx - 1, y = 0, ..., z = nz - 1) holds its cells at a + n1 * b, (a, b)
+// the coordinates on the next two axes; axes of extent 1 have none.
+struct FacePlanes {
+  std::vector<uint8_t> data;
+  long long off[6], n1[6];
+  int at(int f, long long a, long long b) const { return data[(size_t)(off[f] + a + n1[f] * b)]; }
+};
+
+// Boundary faces of a mask (its face planes): a face plane qualifies when none of
 // its cells is fluid-like; its type is that of the plane's centre cell.  A
 // face stays only while every cell of its plane has the type the pull derives
 // from the remaining faces (where planes meet WALL wins, then FWALL; at most
 // one other type among LID / EQ); dropped faces are covered by ghost links
 // and the fix-up list.  Axes of extent 1 carry no faces.
-static void detect_faces(const uint8_t* m, long long nx, long long ny, long long nz, int out[6]) {
+static void detect_faces(const FacePlanes& pl, long long nx, long long ny, long long nz, int out[6]) {
   for (int f = 0; f < 6; ++f) out[f] = 0;
   const long long ext[3] = {nx, ny, nz};
-  auto at = [&](long long x, long long y, long long z) { return (int)m[x + nx * (y + ny * z)]; };
   auto fl = [](int t) { return t == XLB_CELL_FLUID || t == XLB_CELL_INLET || t == XLB_CELL_OUTLET; };
   int cand[6] = {0, 0, 0, 0, 0, 0};
   for (int f = 0; f < 6; ++f) {
@@ -434,21 +443,12 @@ static void detect_faces(const uint8_t* m, long long nx, long long ny, long long
     if (ext[ax] < 2) continue;
     const long long pos = (f % 2) ? ext[ax] - 1 : 0;
     const long long n1 = ext[(ax + 1) % 3], n2 = ext[(ax + 2) % 3];
+    (void)pos;
     bool ok = true;
     for (long long a = 0; a < n1 && ok; ++a)
-      for (long long b = 0; b < n2 && ok; ++b) {
-        long long q[3];
-        q[ax] = pos;
-        q[(ax + 1) % 3] = a;
-        q[(ax + 2) % 3] = b;
-        ok = !fl(at(q[0], q[1], q[2]));
-      }
+      for (long long b = 0; b < n2 && ok; ++b) ok = !fl(pl.at(f, a, b));
     if (!ok) continue;
-    long long q[3];
-    q[ax] = pos;
-    q[(ax + 1) % 3] = n1 / 2;
-    q[(ax + 2) % 3] = n2 / 2;
-    const int t = at(q[0], q[1], q[2]);
+    const int t = pl.at(f, n1 / 2, n2 / 2);
     if (t == XLB_CELL_WALL || t == XLB_CELL_LID || t == XLB_CELL_EQ || t == XLB_CELL_FWALL) cand[f] = t;
   }
   int other = 0;
@@ -487,7 +487,7 @@ static void detect_faces(const uint8_t* m, long long nx, long long ny, long long
                 to = cand[g];
             }
           }
-          bad = at(q[0], q[1], q[2]) != (tw ? tw : (tf ? tf : to));
+          bad = pl.at(f, a, b) != (tw ? tw : (tf ? tf : to));
         }
       if (bad) {
         cand[f] = 0;
@@ -641,7 +641,7 @@ void xlb_destroy(xlb_ctx* c) {
 // sources lie in the cell's own column), and those cells leave the fix-up
 // list: the strided x-planes are then written only by the coalesced rows of
 // the bulk pass.
-static void detect_io_planes(const uint8_t* m, long long nx, long long ny, long long nz, const int face[6],
+static void detect_io_planes(const FacePlanes& pl, long long nx, long long ny, long long nz, const int face[6],
                              bool* x_in, bool* x_out) {
   *x_in = *x_out = false;
   if (nx < 3) return;
@@ -652,9 +652,8 @@ static void detect_io_planes(const uint8_t* m, long long nx, long long ny, long 
                          (nz > 1 && z == nz - 1 && face[5]);
       if (on_yz) continue;
       any = true;
-      const long long r = nx * (y + ny * z);
-      in_ok = in_ok && m[r] == XLB_CELL_INLET;
-      out_ok = out_ok && m[r + nx - 1] == XLB_CELL_OUTLET;
+      in_ok = in_ok && pl.at(0, y, z) == XLB_CELL_INLET;
+      out_ok = out_ok && pl.at(1, y, z) == XLB_CELL_OUTLET;
     }
   *x_in = any && in_ok;
   *x_out = any && out_ok;
@@ -696,18 +695,34 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
   // inlet / outlet / FWALL cells anywhere (the adjoint support check), from
   // the preparation kernel; the boundary faces, from the mask's face planes
   {
-    std::vector<uint8_t> h;
-    const uint8_t* hp = mask;
-    if (!host_mask) {
-      h.resize(n);
-      CK(cudaMemcpy(h.data(), mask, n, cudaMemcpyDeviceToHost));
-      hp = h.data();
+    FacePlanes pl;
+    const long long ext[3] = {c->nx, c->ny, c->nz};
+    long long tot = 0;
+    for (int f = 0; f < 6; ++f) {
+      const int ax = f / 2;
+      pl.off[f] = tot;
+      pl.n1[f] = ext[(ax + 1) % 3];
+      if (ext[ax] >= 2) tot += ext[(ax + 1) % 3] * ext[(ax + 2) % 3];
+    }
+    pl.data.resize((size_t)tot);
+    if (tot > 0) {
+      uint8_t* dp = nullptr;
+      CK(cudaMalloc(&dp, (size_t)tot));
+      cudaError_t e = launch_extract_planes(dmask, (int)c->nx, (int)c->ny, (int)c->nz, dp, c->stream) != 0
+                          ? cudaErrorInvalidValue
+                          : cudaMemcpyAsync(pl.data.data(), dp, (size_t)tot, cudaMemcpyDeviceToHost, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      cudaFree(dp);
+      if (e != cudaSuccess) {
+        cudaFree(nf);
+        return cuda_fail(c, e, "face planes");
+      }
     }
     new_io = hw[2] != 0;
-    detect_faces(hp, c->nx, c->ny, c->nz, new_face);
+    detect_faces(pl, c->nx, c->ny, c->nz, new_face);
     bool fw_face = false;  // (the bulk instance for FWALL faces has no inflow / outflow planes)
     for (int f = 0; f < 6; ++f) fw_face |= new_face[f] == XLB_CELL_FWALL;
-    if (new_io && !fw_face) detect_io_planes(hp, c->nx, c->ny, c->nz, new_face, &new_x_inlet, &new_x_outlet);
+    if (new_io && !fw_face) detect_io_planes(pl, c->nx, c->ny, c->nz, new_face, &new_x_inlet, &new_x_outlet);
   }
   // With 16-bit storage the bulk pass is bound by instruction issue, and the
   // x-face rules would run in diverging lanes at both ends of every row: the
@@ -715,9 +730,11 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
   // rows) go to the ghost links instead, written by the boundary pass after
   // each update.  The x-faces still take part in deriving the rule of the
   // cells where planes meet.  Lattices with an FWALL x-face keep the rules in
-  // the pull.  (In-row ghost values in the face cells, which the bulk pass
-  // stores with the row, measured slower: 55.7 k against 59.9 k MLUPS on the
-  // FP16 256^3 cavity.)
+  // the pull.  (Two forms that write these values from the bulk pass itself
+  // measured slower on the FP16 256^3 cavity: ghost values held in each
+  // row's face cell, 55.7 k against 59.9 k MLUPS, and ghost values pushed by
+  // the cells next to the faces, 57.9 k against 58.7 k: both diverge the
+  // lanes at the row ends.)
   const bool new_x_linked = c->esize == 2 && (new_face[0] || new_face[1]) && new_face[0] != XLB_CELL_FWALL &&
                             new_face[1] != XLB_CELL_FWALL;
   int link_face[6];
@@ -736,12 +753,9 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
     std::vector<int> hc(nb * (c->Q + 1));
     std::vector<long long> ho(nb * (c->Q + 1));
     // passes 1..Q-1: links of direction i; pass Q: inlet / outlet cells
-    for (int pass = 1; pass <= c->Q && e == cudaSuccess; ++pass) {
-      const int mode = pass == c->Q ? 1 : 0;
-      if (launch_pred_count(mode, pass, c->Q, link_face, new_x_inlet, new_x_outlet, nf, (int)c->nx, (int)c->ny,
-                            (int)c->nz, counts + nb * pass, c->stream) != 0)
-        e = cudaErrorInvalidValue;
-    }
+    if (e == cudaSuccess && launch_pred_count(c->Q, link_face, new_x_inlet, new_x_outlet, nf, (int)c->nx,
+                                              (int)c->ny, (int)c->nz, counts, c->stream) != 0)
+      e = cudaErrorInvalidValue;
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(hc.data() + nb, counts + nb, sizeof(int) * nb * c->Q, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -759,13 +773,10 @@ int xlb_set_mask(xlb_ctx* c, const uint8_t* mask) {
     if (e == cudaSuccess && nl > 0) e = cudaMalloc(&nlinks, sizeof(int2) * nl);
     if (e == cudaSuccess && nl > 0) e = cudaMalloc(&nlcells, sizeof(int2) * nl);
     if (e == cudaSuccess && nfx > 0) e = cudaMalloc(&nfix, sizeof(int) * nfx);
-    for (int pass = 1; pass <= c->Q && e == cudaSuccess; ++pass) {
-      const int mode = pass == c->Q ? 1 : 0;
-      if ((mode == 0 && nl == 0) || (mode == 1 && nfx == 0)) continue;
-      if (launch_pred_write(mode, pass, c->Q, link_face, new_x_inlet, new_x_outlet, nf, (int)c->nx, (int)c->ny,
-                            (int)c->nz, offs + nb * pass, nlinks, nfix, c->stream) != 0)
-        e = cudaErrorInvalidValue;
-    }
+    if (e == cudaSuccess && nl + nfx > 0 &&
+        launch_pred_write(c->Q, link_face, new_x_inlet, new_x_outlet, nf, (int)c->nx, (int)c->ny, (int)c->nz, offs,
+                          nlinks, nfix, c->stream) != 0)
+      e = cudaErrorInvalidValue;
     if (e == cudaSuccess && nl > 0 &&
         launch_link_cells(c->Q, nlinks, nl, nf, (int)c->nx, (int)c->ny, (int)c->nz, nlcells, c->stream) != 0)
       e = cudaErrorInvalidValue;

@@ -67,6 +67,9 @@ long long row_blocks(const StepParams& p);
 // cell occurs.  Q picks the stencil used for the FLAG_SLOW test.
 int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int ny, int nz, int* err_word,
                         void* stream);
+// The six boundary planes of a device mask into `out` (compact, plane by
+// plane: see the face detection in api.cu).
+int launch_extract_planes(const uint8_t* mask, int nx, int ny, int nz, uint8_t* out, void* stream);
 int launch_reduce_final(const double* partial, long long n, double* out, void* stream);
 // FP64 sum of squares of n floats (device memory) into column 0 of
 // min(ceil(n / 2048), capacity) partial rows (at least 1); returns the rows used.
@@ -83,10 +86,13 @@ long long bnd_list_blocks(long long n);
 // x_in / x_out: the INLET cells of x = 0 / OUTLET cells of x = nx - 1 are
 // served by the bulk pass: they are not fix-up cells, and their links are
 // listed like those of FLUID cells.
-int launch_pred_count(int mode, int dir, int Q, const int* face, bool x_in, bool x_out, const uint8_t* flags, int nx,
-                      int ny, int nz, int* counts, void* stream);
-int launch_pred_write(int mode, int dir, int Q, const int* face, bool x_in, bool x_out, const uint8_t* flags, int nx,
-                      int ny, int nz, const long long* offs, int2* links, int* cells, void* stream);
+// One launch each evaluates every table: counts / offs are indexed
+// [pass * chunks + chunk] (chunks of bnd_list_blocks), pass 1..Q-1 the links
+// of direction pass, pass Q the fix-up cells.
+int launch_pred_count(int Q, const int* face, bool x_in, bool x_out, const uint8_t* flags, int nx, int ny, int nz,
+                      int* counts, void* stream);
+int launch_pred_write(int Q, const int* face, bool x_in, bool x_out, const uint8_t* flags, int nx, int ny, int nz,
+                      const long long* offs, int2* links, int* cells, void* stream);
 // Per link {cell x, dir i | ...}: the source cell x - c_i (periodic) and the
 // cell x + c_i when it is FLUID, else -1 (the boundary pass's Bouzidi partner).
 int launch_link_cells(int Q, const int2* links, long long n, const uint8_t* flags, int nx, int ny, int nz,

@@ -33,42 +33,49 @@ __device__ __forceinline__ void cell_xyz(long long cell, int nx, int ny, bool sm
 template <int Q>
 __global__ void k_mask_prepare(const uint8_t* __restrict__ mask, uint8_t* __restrict__ flags, int nx, int ny,
                                int nz, int* err) {
-  const long long n = (long long)nx * ny * nz;
-  const bool small = n < 0x7fffffffLL;
+  // blocks stride over the rows (y, z), threads over x: no division per cell
+  const long long rows = (long long)ny * nz;
   bool io = false;
-  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
-       cell += (long long)gridDim.x * blockDim.x) {
-    const int t = mask[cell];
-    if (t > FWALL) {
-      atomicExch(err, 1);
-      flags[cell] = WALL;
-      continue;
-    }
-    int slow = (t == INLET || t == OUTLET || t == FWALL);
-    io |= slow != 0;
-    if (fluid_like(t) && !slow) {
-      int x, y, z;
-      cell_xyz(cell, nx, ny, small, x, y, z);
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int y = (int)(row % ny), z = (int)(row / ny);
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    const uint8_t* rb[3][3];
+    {
+      const int ys[3] = {ym, y, yp}, zs[3] = {zm, z, zp};
 #pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        int xs = x - Lattice<Q>::c(i, 0), ys = y - Lattice<Q>::c(i, 1), zs = z - Lattice<Q>::c(i, 2);
-        xs = xs < 0 ? nx - 1 : (xs >= nx ? 0 : xs);
-        ys = ys < 0 ? ny - 1 : (ys >= ny ? 0 : ys);
-        zs = zs < 0 ? nz - 1 : (zs >= nz ? 0 : zs);
-        const int ts = mask[xs + (long long)nx * (ys + (long long)ny * zs)];
-        if (!holds_state(ts)) slow = 1;
-      }
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rb[b][c] = mask + (long long)nx * (ys[b] + (long long)ny * zs[c]);
     }
-    flags[cell] = (uint8_t)(t | (slow ? FLAG_SLOW : 0));
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      const long long cell = x + (long long)nx * row;
+      const int t = mask[cell];
+      if (t > FWALL) {
+        atomicExch(err, 1);
+        flags[cell] = WALL;
+        continue;
+      }
+      int slow = (t == INLET || t == OUTLET || t == FWALL);
+      io |= slow != 0;
+      if (fluid_like(t) && !slow) {
+        const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const int ts = rb[1 - Lattice<Q>::c(i, 1)][1 - Lattice<Q>::c(i, 2)][xs[1 - Lattice<Q>::c(i, 0)]];
+          if (!holds_state(ts)) slow = 1;
+        }
+      }
+      flags[cell] = (uint8_t)(t | (slow ? FLAG_SLOW : 0));
+    }
   }
   if (io) atomicOr(err + 2, 1);
 }
 
 int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int ny, int nz, int* err,
                         void* stream) {
-  const long long n = (long long)nx * ny * nz;
-  long long blocks = (n + 255) / 256;
-  if (blocks > 152LL * 64) blocks = 152LL * 64;
+  const long long rows = (long long)ny * nz;
+  long long blocks = rows < 152LL * 64 ? rows : 152LL * 64;
   if (blocks < 1) blocks = 1;
   cudaStream_t s = (cudaStream_t)stream;
   if (Q == 9)
@@ -82,9 +89,10 @@ int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int 
   return 0;
 }
 
-// Boundary tables, built once per mask by compaction in two passes per
-// table (per-block counts; an exclusive scan of the counts on the host; then
-// ordered per-block writes):
+// Boundary tables, built once per mask by compaction in two launches over
+// chunks of consecutive cells, each evaluating every table for its cells
+// (per-chunk counts; an exclusive scan of the counts on the host; then
+// ordered per-chunk writes):
 //  - links, direction-major: for each direction i in turn, every FLUID cell,
 //    every FWALL cell on an FWALL face plane and every inlet / outlet cell the
 //    bulk pass serves, x (ascending), whose source x - c_i is WALL, LID or EQ
@@ -96,8 +104,6 @@ int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int 
 constexpr int LIST_BLOCK = 256;
 
 struct Pred {
-  int mode;        // 0: link in direction (cx, cy, cz); 1: fix-up cell
-  int cx, cy, cz;  // velocity of the link direction
   int face[6];     // described boundary faces: their sources need no ghost
   int x_in, x_out; // INLET cells of x = 0 / OUTLET cells of x = nx - 1 served by the bulk pass
 };
@@ -108,116 +114,172 @@ __device__ __forceinline__ bool on_face_plane(int x, int y, int z, int nx, int n
          (y == ny - 1 && pr.face[3]) || (nz > 1 && z == 0 && pr.face[4]) || (nz > 1 && z == nz - 1 && pr.face[5]);
 }
 
-__device__ __forceinline__ int pred_eval(const uint8_t* __restrict__ flags, long long cell, int nx, int ny, int nz,
-                                         const Pred& pr, int* type) {
+// Every table entry of one cell at once: bit i (1 <= i < Q) of the result
+// says that the cell owns a link in direction i (types[i] = the source's
+// type), bit Q that it is a fix-up cell.  The coordinates are found once and
+// the Q - 1 neighbour flags are loaded together.
+template <int Q>
+__device__ __forceinline__ uint32_t cell_preds(const uint8_t* __restrict__ flags, long long cell, long long n, int nx,
+                                               int ny, int nz, const Pred& pr, uint8_t (&types)[Q]) {
+  // only FLUID cells with a WALL / LID / EQ neighbour and INLET / OUTLET /
+  // FWALL cells carry FLAG_SLOW; every other cell has no entry
+  if (cell >= n) return 0u;
   const int fl = flags[cell];
+  if (!(fl & FLAG_SLOW)) return 0u;
   const int t = fl & FLAG_TYPE;
-  if (!(t == FLUID || t == FWALL || t == INLET || t == OUTLET)) return 0;
-  if (pr.mode == 1 && t == FLUID) return 0;
-  if (!(fl & FLAG_SLOW)) return 0;  // a FLUID cell with no WALL / LID / EQ source
+  if (!(t == FLUID || t == FWALL || t == INLET || t == OUTLET)) return 0u;
   int x, y, z;
   cell_xyz(cell, nx, ny, (long long)nx * ny * nz < 0x7fffffffLL, x, y, z);
   // inlet / outlet cells on the x-planes the bulk pass serves
   const bool io_bulk = (t == INLET && pr.x_in && x == 0) || (t == OUTLET && pr.x_out && x == nx - 1);
-  if (pr.mode == 0 && (t == INLET || t == OUTLET) && !io_bulk) return 0;
   // an FWALL cell on a face plane is updated by the bulk pass (it lies on an
   // FWALL face: the host keeps a face only where its plane's cells have the
   // type the faces derive); any other FWALL cell is a fix-up cell
   const bool fw_face = t == FWALL && on_face_plane(x, y, z, nx, ny, nz, pr);
-  if (pr.mode == 1) return ((t == INLET || t == OUTLET) && !io_bulk) || (t == FWALL && !fw_face);
-  if (t == FWALL && !fw_face) return 0;
-  int xs = x - pr.cx, ys = y - pr.cy, zs = z - pr.cz;
-  xs = xs < 0 ? nx - 1 : (xs >= nx ? 0 : xs);
-  ys = ys < 0 ? ny - 1 : (ys >= ny ? 0 : ys);
-  zs = zs < 0 ? nz - 1 : (zs >= nz ? 0 : zs);
-  const int ts = flags[xs + (long long)nx * (ys + (long long)ny * zs)] & FLAG_TYPE;
-  *type = ts;
-  return !holds_state(ts) && !on_face_plane(xs, ys, zs, nx, ny, nz, pr);
-}
-
-__global__ void k_pred_count(const uint8_t* __restrict__ flags, long long n, int nx, int ny, int nz, Pred pr,
-                             int* counts) {
-  const long long cell = blockIdx.x * (long long)LIST_BLOCK + threadIdx.x;
-  int t = 0;
-  const int hit = cell < n ? pred_eval(flags, cell, nx, ny, nz, pr, &t) : 0;
-  const int c = __syncthreads_count(hit);
-  if (threadIdx.x == 0) counts[blockIdx.x] = c;
-}
-
-__global__ void k_pred_write(const uint8_t* __restrict__ flags, long long n, int nx, int ny, int nz, Pred pr,
-                             int dir, const long long* __restrict__ offs, int2* links, int* cells) {
-  __shared__ int warp_base[LIST_BLOCK / 32];
-  const long long cell = blockIdx.x * (long long)LIST_BLOCK + threadIdx.x;
-  int t = 0;
-  const int hit = cell < n ? pred_eval(flags, cell, nx, ny, nz, pr, &t) : 0;
-  const unsigned ballot = __ballot_sync(0xffffffffu, hit);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) warp_base[warp] = __popc(ballot);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int w = 0; w < LIST_BLOCK / 32; ++w) {
-      const int c = warp_base[w];
-      warp_base[w] = run;
-      run += c;
+  const bool fix = ((t == INLET || t == OUTLET) && !io_bulk) || (t == FWALL && !fw_face);
+  uint32_t bits = fix ? 1u << Q : 0u;
+  if (!(t == FLUID || fw_face || io_bulk)) return bits;
+  const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+  const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+  const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+  int ts[Q];
+#pragma unroll
+  for (int i = 1; i < Q; ++i)
+    ts[i] = flags[xs[1 - Lattice<Q>::c(i, 0)] +
+                  (long long)nx * (ys[1 - Lattice<Q>::c(i, 1)] + (long long)ny * zs[1 - Lattice<Q>::c(i, 2)])] &
+            FLAG_TYPE;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int sx = xs[1 - Lattice<Q>::c(i, 0)], sy = ys[1 - Lattice<Q>::c(i, 1)], sz = zs[1 - Lattice<Q>::c(i, 2)];
+    if (!holds_state(ts[i]) && !on_face_plane(sx, sy, sz, nx, ny, nz, pr)) {
+      bits |= 1u << i;
+      types[i] = (uint8_t)ts[i];
     }
   }
-  __syncthreads();
-  if (hit) {
-    const long long o = offs[blockIdx.x] + warp_base[warp] + __popc(ballot & ((1u << lane) - 1u));
-    if (pr.mode == 1)
-      cells[o] = (int)cell;
-    else
-      links[o] = make_int2((int)cell, dir | (t << 8));
+  return bits;
+}
+
+// Chunks of LIST_SUB x LIST_BLOCK consecutive cells, taken by a block in
+// LIST_SUB rounds of LIST_BLOCK cells (ascending), so that the host scans one
+// count per chunk and table.
+constexpr int LIST_SUB = 16;
+
+template <int Q>
+__global__ void k_pred_count(const uint8_t* __restrict__ flags, long long n, int nx, int ny, int nz, Pred pr,
+                             long long nchunks, int* counts) {
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    int acc[Q + 1];
+#pragma unroll
+    for (int pass = 0; pass <= Q; ++pass) acc[pass] = 0;
+    for (int sub = 0; sub < LIST_SUB; ++sub) {
+      uint8_t types[Q];
+      const long long cell = (chunk * LIST_SUB + sub) * LIST_BLOCK + threadIdx.x;
+      const uint32_t bits = cell_preds<Q>(flags, cell, n, nx, ny, nz, pr, types);
+      if (!__syncthreads_or(bits != 0u)) continue;
+#pragma unroll
+      for (int pass = 1; pass <= Q; ++pass) acc[pass] += __syncthreads_count((bits >> pass) & 1u);
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int pass = 1; pass <= Q; ++pass) counts[nchunks * pass + chunk] = acc[pass];
+    }
   }
 }
 
-long long bnd_list_blocks(long long n) { return (n + LIST_BLOCK - 1) / LIST_BLOCK; }
+template <int Q>
+__global__ void k_pred_write(const uint8_t* __restrict__ flags, long long n, int nx, int ny, int nz, Pred pr,
+                             long long nchunks, const long long* __restrict__ offs, int2* links, int* cells) {
+  __shared__ int warp_base[LIST_BLOCK / 32];
+  __shared__ int round_total;
+  __shared__ long long next[Q + 1];  // the next entry of each table in this chunk
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    __syncthreads();  // next[] of the previous chunk has been read
+    if (threadIdx.x <= Q && threadIdx.x > 0) next[threadIdx.x] = offs[nchunks * threadIdx.x + chunk];
+    __syncthreads();
+    for (int sub = 0; sub < LIST_SUB; ++sub) {
+      const long long cell = (chunk * LIST_SUB + sub) * LIST_BLOCK + threadIdx.x;
+      uint8_t types[Q];
+      const uint32_t bits = cell_preds<Q>(flags, cell, n, nx, ny, nz, pr, types);
+      if (!__syncthreads_or(bits != 0u)) continue;
+#pragma unroll
+      for (int pass = 1; pass <= Q; ++pass) {
+        const int hit = (bits >> pass) & 1u;
+        const unsigned ballot = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) warp_base[warp] = __popc(ballot);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          int run = 0;
+          for (int w = 0; w < LIST_BLOCK / 32; ++w) {
+            const int c = warp_base[w];
+            warp_base[w] = run;
+            run += c;
+          }
+          round_total = run;
+        }
+        __syncthreads();
+        if (hit) {
+          const long long o = next[pass] + warp_base[warp] + __popc(ballot & ((1u << lane) - 1u));
+          if (pass == Q)
+            cells[o] = (int)cell;
+          else
+            links[o] = make_int2((int)cell, pass | (types[pass] << 8));
+        }
+        __syncthreads();  // every thread has read warp_base and next[pass]
+        if (threadIdx.x == 0) next[pass] += round_total;
+      }
+      __syncthreads();
+    }
+  }
+}
 
-static Pred make_pred(int mode, int dir, int Q, const int* face, bool x_in, bool x_out) {
+long long bnd_list_blocks(long long n) { return (n + LIST_BLOCK * LIST_SUB - 1) / (LIST_BLOCK * LIST_SUB); }
+
+static Pred make_pred(const int* face, bool x_in, bool x_out) {
   Pred pr;
-  pr.mode = mode;
   pr.x_in = x_in ? 1 : 0;
   pr.x_out = x_out ? 1 : 0;
-  pr.cx = pr.cy = pr.cz = 0;
   for (int f = 0; f < 6; ++f) pr.face[f] = face ? face[f] : 0;
-  if (mode == 0) {
-    if (Q == 9) {
-      pr.cx = Lattice<9>::c(dir, 0);
-      pr.cy = Lattice<9>::c(dir, 1);
-    }
-    if (Q == 19) {
-      pr.cx = Lattice<19>::c(dir, 0);
-      pr.cy = Lattice<19>::c(dir, 1);
-      pr.cz = Lattice<19>::c(dir, 2);
-    }
-    if (Q == 27) {
-      pr.cx = Lattice<27>::c(dir, 0);
-      pr.cy = Lattice<27>::c(dir, 1);
-      pr.cz = Lattice<27>::c(dir, 2);
-    }
-  }
   return pr;
 }
 
-int launch_pred_count(int mode, int dir, int Q, const int* face, bool x_in, bool x_out, const uint8_t* flags, int nx,
-                      int ny, int nz, int* counts, void* stream) {
+static long long pred_grid(long long nchunks) { return nchunks < 152LL * 16 ? nchunks : 152LL * 16; }
+
+int launch_pred_count(int Q, const int* face, bool x_in, bool x_out, const uint8_t* flags, int nx, int ny, int nz,
+                      int* counts, void* stream) {
   const long long n = (long long)nx * ny * nz;
-  const long long b = bnd_list_blocks(n);
-  if (b > 0x7fffffffLL) return -1;
-  const Pred pr = make_pred(mode, dir, Q, face, x_in, x_out);
-  k_pred_count<<<(unsigned)b, LIST_BLOCK, 0, (cudaStream_t)stream>>>(flags, n, nx, ny, nz, pr, counts);
+  const long long nc = bnd_list_blocks(n);
+  if (nc < 1) return 0;
+  const Pred pr = make_pred(face, x_in, x_out);
+  const unsigned g = (unsigned)pred_grid(nc);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (Q == 9)
+    k_pred_count<9><<<g, LIST_BLOCK, 0, s>>>(flags, n, nx, ny, nz, pr, nc, counts);
+  else if (Q == 19)
+    k_pred_count<19><<<g, LIST_BLOCK, 0, s>>>(flags, n, nx, ny, nz, pr, nc, counts);
+  else if (Q == 27)
+    k_pred_count<27><<<g, LIST_BLOCK, 0, s>>>(flags, n, nx, ny, nz, pr, nc, counts);
+  else
+    return -1;
   return 0;
 }
 
-int launch_pred_write(int mode, int dir, int Q, const int* face, bool x_in, bool x_out, const uint8_t* flags, int nx,
-                      int ny, int nz, const long long* offs, int2* links, int* cells, void* stream) {
+int launch_pred_write(int Q, const int* face, bool x_in, bool x_out, const uint8_t* flags, int nx, int ny, int nz,
+                      const long long* offs, int2* links, int* cells, void* stream) {
   const long long n = (long long)nx * ny * nz;
-  const long long b = bnd_list_blocks(n);
-  if (b > 0x7fffffffLL) return -1;
-  const Pred pr = make_pred(mode, dir, Q, face, x_in, x_out);
-  k_pred_write<<<(unsigned)b, LIST_BLOCK, 0, (cudaStream_t)stream>>>(flags, n, nx, ny, nz, pr, dir, offs, links,
-                                                                     cells);
+  const long long nc = bnd_list_blocks(n);
+  if (nc < 1) return 0;
+  const Pred pr = make_pred(face, x_in, x_out);
+  const unsigned g = (unsigned)pred_grid(nc);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (Q == 9)
+    k_pred_write<9><<<g, LIST_BLOCK, 0, s>>>(flags, n, nx, ny, nz, pr, nc, offs, links, cells);
+  else if (Q == 19)
+    k_pred_write<19><<<g, LIST_BLOCK, 0, s>>>(flags, n, nx, ny, nz, pr, nc, offs, links, cells);
+  else if (Q == 27)
+    k_pred_write<27><<<g, LIST_BLOCK, 0, s>>>(flags, n, nx, ny, nz, pr, nc, offs, links, cells);
+  else
+    return -1;
   return 0;
 }
 
@@ -259,6 +321,36 @@ int launch_link_cells(int Q, const int2* links, long long n, const uint8_t* flag
     k_link_cells<27><<<(unsigned)blocks, 256, 0, s>>>(links, n, flags, nx, ny, nz, cells);
   else
     return -1;
+  return 0;
+}
+
+// The six boundary planes of a mask in one compact buffer: plane f (axis
+// f / 2 at 0 or n - 1) holds its cells at a + n1 * b, (a, b) the coordinates
+// on axes (f / 2 + 1) % 3 and (f / 2 + 2) % 3; axes of extent 1 have none.
+__global__ void k_extract_planes(const uint8_t* __restrict__ mask, int nx, int ny, int nz, uint8_t* __restrict__ out) {
+  const long long ext[3] = {nx, ny, nz};
+  long long off = 0;
+  for (int f = 0; f < 6; ++f) {
+    const int ax = f / 2;
+    if (ext[ax] < 2) continue;
+    const long long n1 = ext[(ax + 1) % 3], n2 = ext[(ax + 2) % 3], pos = (f % 2) ? ext[ax] - 1 : 0;
+    for (long long k = blockIdx.x * 256LL + threadIdx.x; k < n1 * n2; k += (long long)gridDim.x * 256) {
+      long long q[3];
+      q[ax] = pos;
+      q[(ax + 1) % 3] = k % n1;
+      q[(ax + 2) % 3] = k / n1;
+      out[off + k] = mask[q[0] + nx * (q[1] + (long long)ny * q[2])];
+    }
+    off += n1 * n2;
+  }
+}
+
+int launch_extract_planes(const uint8_t* mask, int nx, int ny, int nz, uint8_t* out, void* stream) {
+  const long long big = (long long)(nx > ny ? nx : ny) * (ny > nz ? ny : nz) * 2;
+  long long blocks = (big + 255) / 256;
+  if (blocks > 152LL * 8) blocks = 152LL * 8;
+  if (blocks < 1) blocks = 1;
+  k_extract_planes<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(mask, nx, ny, nz, out);
   return 0;
 }
 
