@@ -129,13 +129,14 @@ int xlb_set_mask(xlb_ctx* ctx, const uint8_t* mask);
  * and OUTLET planes at x = nx - 1 (apart from cells on y / z faces) are
  * updated by the bulk pass; their cells then count as link owners, not as
  * fix-up cells.
- * n_links = number of (cell, direction) pairs, over FLUID cells
- * and FWALL cells of FWALL face planes, whose source cell is WALL, LID or EQ
- * off the face planes; n_fix = number of INLET and OUTLET cells plus the
- * FWALL cells off the face planes.  After each update a boundary pass
- * writes, for every link, the value the rule prescribes into the source
- * cell's slot for that direction (a ghost value, so the next update can pull
- * every cell as if periodic) and recomputes the fix-up cells. */
+ * n_links = number of (cell, direction) pairs, over FLUID cells, FWALL
+ * cells of FWALL face planes and the cells of those inlet / outlet planes,
+ * whose source cell is WALL, LID or EQ off the face planes; n_fix = number
+ * of the other INLET and OUTLET cells plus the FWALL cells off the face
+ * planes.  After each update a boundary pass writes, for every link, the
+ * value the rule prescribes into the source cell's slot for that direction
+ * (a ghost value, so the next update can pull every cell as if periodic)
+ * and stores the fix-up cells, recomputed beside the bulk pass. */
 int xlb_boundary_links(const xlb_ctx* ctx, int64_t* n_links, int64_t* n_fix);
 
 /* Zou-He inlet velocity per cell (a velocity profile, e.g. the Poiseuille

@@ -46,7 +46,7 @@ struct xlb_ctx {
   int2* links = nullptr;  // ghost links {cell, dir | type << 8} of the mask
   long long n_links = 0;
   int2* link_cells = nullptr;        // per link: source cell, Bouzidi partner (k_link_cells)
-  int* fix = nullptr;  // inlet / outlet cells (recomputed after a bulk pass)
+  int* fix = nullptr;  // fix-up cells: inlet / outlet cells off whole x-planes, FWALL cells off the faces
   long long n_fix = 0;
   void* fix_side = nullptr;  // Q x n_fix values of the storage type: their recomputed update
   // auxiliary stream on which the fix-up cells are recomputed beside the bulk
@@ -327,9 +327,11 @@ static int boundary_pass(xlb_ctx* c, const void* fix_src, void* dst, bool from_s
 
 // One lattice update from buffer src to dst (either the live pair or tape
 // slots): a bulk pass that pulls every cell as if periodic (no flag reads) --
-// the wall, lid and EQ cells hold ghost values that make that pull exact --
+// the wall, lid and EQ cells hold ghost values that make that pull exact;
+// whole inlet / outlet x-planes take their rules in the bulk pass too --
 // then the boundary pass, which rewrites the ghosts for the next step and
-// recomputes the inlet / outlet cells.
+// stores the other fix-up cells (inlet / outlet cells off those planes,
+// FWALL cells off the faces).
 // The fix-up cells' recomputation reads only src, so it runs on the
 // auxiliary stream beside the bulk pass (forked from and joined back to the
 // ctx stream by events, which a graph capture turns into parallel branches)
