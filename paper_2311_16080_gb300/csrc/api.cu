@@ -142,6 +142,20 @@ static bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Page-locked host memory mapped into the device's address space (what
+// cudaHostAlloc / cudaHostRegister give with unified addressing): kernels
+// read and write it over the host link themselves, which on this platform
+// moves a field faster than a staged copy-engine transfer.  Returns the
+// device-side pointer, or null for any other memory.
+static void* mapped_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 static size_t state_elems(const xlb_ctx* c) { return (size_t)c->Q * (size_t)c->plane; }
 static size_t state_bytes_raw(const xlb_ctx* c) { return state_elems(c) * (size_t)c->esize; }
 
@@ -1020,15 +1034,23 @@ int xlb_init(xlb_ctx* c, const float* rho, const float* u) {
   const size_t n = (size_t)c->N;
   float* dr = c->init_fields;
   float* du = c->init_fields + n;
-  // copy the caller's fields into the library-owned init fields
-  if (rho) {
+  // copy the caller's fields into the library-owned init fields (mapped
+  // page-locked host memory: by a copy kernel that reads it directly)
+  void* mr = mapped_host_ptr(rho);
+  void* mu = mapped_host_ptr(u);
+  if (rho && mr) {
+    if (launch_copy_f32((const float*)mr, dr, (long long)n, c->stream) != 0) return fail(c, XLB_ERR_CUDA, "copy");
+  } else if (rho) {
     CK(cudaMemcpyAsync(dr, rho, n * sizeof(float), cudaMemcpyDefault, c->stream));
   } else {
     std::vector<float> ones(n, 1.0f);
     CK(cudaMemcpyAsync(dr, ones.data(), n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
-  if (u) {
+  if (u && mu) {
+    if (launch_copy_f32((const float*)mu, du, (long long)c->D * (long long)n, c->stream) != 0)
+      return fail(c, XLB_ERR_CUDA, "copy");
+  } else if (u) {
     CK(cudaMemcpyAsync(du, u, (size_t)c->D * n * sizeof(float), cudaMemcpyDefault, c->stream));
   } else {
     CK(cudaMemsetAsync(du, 0, (size_t)c->D * n * sizeof(float), c->stream));
@@ -1176,9 +1198,17 @@ int xlb_macroscopic(xlb_ctx* c, float* rho, float* u) {
   if (!c) return XLB_ERR_ARG;
   if (!rho && !u) return XLB_OK;
   const size_t n = (size_t)c->N;
-  const bool host = !is_device_ptr(rho ? (void*)rho : (void*)u);
+  bool host = !is_device_ptr(rho ? (void*)rho : (void*)u);
   float* dr = rho;
   float* du = u;
+  // mapped page-locked host memory: the readout kernel writes it directly
+  float* mr = (float*)mapped_host_ptr(rho);
+  float* mu = (float*)mapped_host_ptr(u);
+  if (host && (!rho || mr) && (!u || mu)) {
+    dr = mr;
+    du = mu;
+    host = false;  // nothing to copy; check_device_error below synchronises the stream
+  }
   if (host) {
     int r = ensure_stage(c, (1 + c->D) * n * sizeof(float));
     if (r) return r;

@@ -70,6 +70,8 @@ int launch_mask_prepare(int Q, const uint8_t* mask, uint8_t* flags, int nx, int 
 // The six boundary planes of a device mask into `out` (compact, plane by
 // plane: see the face detection in api.cu).
 int launch_extract_planes(const uint8_t* mask, int nx, int ny, int nz, uint8_t* out, void* stream);
+// n floats from src to dst by a kernel (src or dst may be mapped host memory).
+int launch_copy_f32(const float* src, float* dst, long long n, void* stream);
 int launch_reduce_final(const double* partial, long long n, double* out, void* stream);
 // FP64 sum of squares of n floats (device memory) into column 0 of
 // min(ceil(n / 2048), capacity) partial rows (at least 1); returns the rows used.

@@ -354,6 +354,30 @@ int launch_extract_planes(const uint8_t* mask, int nx, int ny, int nz, uint8_t* 
   return 0;
 }
 
+// n floats from src to dst (either may be mapped host memory), 16 bytes per
+// access where both are 16-byte aligned.
+__global__ void k_copy_f32(const float* __restrict__ src, float* __restrict__ dst, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0) {
+    const long long n4 = n / 4;
+    for (long long k = t; k < n4; k += stride)
+      reinterpret_cast<float4*>(dst)[k] = reinterpret_cast<const float4*>(src)[k];
+    for (long long k = 4 * n4 + t; k < n; k += stride) dst[k] = src[k];
+  } else {
+    for (long long k = t; k < n; k += stride) dst[k] = src[k];
+  }
+}
+
+int launch_copy_f32(const float* src, float* dst, long long n, void* stream) {
+  if (n <= 0) return 0;
+  long long blocks = (n / 4 + 255) / 256;
+  if (blocks > 152LL * 8) blocks = 152LL * 8;
+  if (blocks < 1) blocks = 1;
+  k_copy_f32<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(src, dst, n);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 // Sums n rows of 4 doubles in a fixed order (deterministic): each thread
 // strides over rows, then a fixed shared-memory tree.
 __global__ void k_reduce_final(const double* __restrict__ partial, long long n, double* out) {
