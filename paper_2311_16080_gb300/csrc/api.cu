@@ -461,8 +461,8 @@ static void detect_faces(const FacePlanes& pl, long long nx, long long ny, long 
     const long long n1 = ext[(ax + 1) % 3], n2 = ext[(ax + 2) % 3];
     (void)pos;
     bool ok = true;
-    for (long long a = 0; a < n1 && ok; ++a)
-      for (long long b = 0; b < n2 && ok; ++b) ok = !fl(pl.at(f, a, b));
+    for (long long b = 0; b < n2 && ok; ++b)
+      for (long long a = 0; a < n1 && ok; ++a) ok = !fl(pl.at(f, a, b));
     if (!ok) continue;
     const int t = pl.at(f, n1 / 2, n2 / 2);
     if (t == XLB_CELL_WALL || t == XLB_CELL_LID || t == XLB_CELL_EQ || t == XLB_CELL_FWALL) cand[f] = t;
@@ -483,27 +483,32 @@ static void detect_faces(const FacePlanes& pl, long long nx, long long ny, long 
       const long long pos = (f % 2) ? ext[ax] - 1 : 0;
       const long long n1 = ext[(ax + 1) % 3], n2 = ext[(ax + 2) % 3];
       bool bad = false;
-      for (long long a = 0; a < n1 && !bad; ++a)
-        for (long long b = 0; b < n2 && !bad; ++b) {
-          long long q[3];
-          q[ax] = pos;
-          q[(ax + 1) % 3] = a;
-          q[(ax + 2) % 3] = b;
-          int tw = 0, tf = 0, to = 0;
-          for (int g = 0; g < 6; ++g) {
-            if (!cand[g]) continue;
-            const int gx = g / 2;
-            const long long gp = (g % 2) ? ext[gx] - 1 : 0;
-            if (q[gx] == gp) {
-              if (cand[g] == XLB_CELL_WALL)
-                tw = XLB_CELL_WALL;
-              else if (cand[g] == XLB_CELL_FWALL)
-                tf = XLB_CELL_FWALL;
-              else
-                to = cand[g];
+      for (long long b = 0; b < n2 && !bad; ++b)
+        for (long long a = 0; a < n1 && !bad; ++a) {
+          // a cell off the plane's border lies on no other face plane
+          int want = cand[f];
+          if (a == 0 || a == n1 - 1 || b == 0 || b == n2 - 1) {
+            long long q[3];
+            q[ax] = pos;
+            q[(ax + 1) % 3] = a;
+            q[(ax + 2) % 3] = b;
+            int tw = 0, tf = 0, to = 0;
+            for (int g = 0; g < 6; ++g) {
+              if (!cand[g]) continue;
+              const int gx = g / 2;
+              const long long gp = (g % 2) ? ext[gx] - 1 : 0;
+              if (q[gx] == gp) {
+                if (cand[g] == XLB_CELL_WALL)
+                  tw = XLB_CELL_WALL;
+                else if (cand[g] == XLB_CELL_FWALL)
+                  tf = XLB_CELL_FWALL;
+                else
+                  to = cand[g];
+              }
             }
+            want = tw ? tw : (tf ? tf : to);
           }
-          bad = pl.at(f, a, b) != (tw ? tw : (tf ? tf : to));
+          bad = pl.at(f, a, b) != want;
         }
       if (bad) {
         cand[f] = 0;
